@@ -1,0 +1,204 @@
+"""Python access to the FP64 CPU oracle (``nrc_oracle.cpp``).
+
+TEST INFRASTRUCTURE.  Only the tests, the package's smoke check and the
+benchmark's CPU-baseline leg may import this module.  The CUDA library and its
+binding never import it; the two implementations share no code.
+
+Every function takes numpy arrays, promotes FP32 inputs to FP64 exactly as the
+C code does, and returns FP64 results.  See the C source for the passage of
+the paper each step follows.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "nrc_oracle.cpp")
+_LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+ENC_CHEAP, ENC_EXACT = 0, 1
+LOSS_LUMINANCE, LOSS_PER_CHANNEL = 0, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with g++ (no -ffast-math, no FMA contraction)."""
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-pthread",
+                               _SRC, "-o", tmp])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            L = ctypes.CDLL(path)
+            P = ctypes.c_void_p
+            i64, u64, i32, f64 = ctypes.c_int64, ctypes.c_uint64, ctypes.c_int, ctypes.c_double
+            sig = {
+                "oracle_abi_version": (i32, []),
+                "oracle_lcg_params": (None, [i64, u64, P, P]),
+                "oracle_permutation": (None, [i64, u64, P]),
+                "oracle_gather": (None, [P, P, i64, i64, u64, i32, P, P, P]),
+                "oracle_tri": (f64, [f64]),
+                "oracle_quartic": (f64, [f64]),
+                "oracle_quartic_cdf": (f64, [f64]),
+                "oracle_freq_feature": (f64, [f64, i32, i32]),
+                "oracle_oneblob": (None, [f64, i32, i32, P]),
+                "oracle_encode": (None, [P, i64, i32, f64, P]),
+                "oracle_forward": (None, [P, P, i32, P, i64, P, P]),
+                "oracle_loss": (f64, [P, P, i64, i32, f64, P]),
+                "oracle_backward": (None, [P, P, i32, P, P, i64, P]),
+                "oracle_adam": (None, [P, P, P, P, i64, i64, f64, f64, f64, f64]),
+                "oracle_infer": (None, [P, P, i32, P, i64, i32, f64, P]),
+                "oracle_train_step": (f64, [P, P, P, P, P, i32, P, P, i64, i64, u64, i32, i32, f64, i32, f64,
+                                            f64, f64, f64, f64, P]),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f32(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _dims(dims) -> np.ndarray:
+    return np.ascontiguousarray(dims, dtype=np.int32)
+
+
+# ---------------------------------------------------------------- primitives
+def tri(x: float) -> float:
+    return lib().oracle_tri(float(x))
+
+
+def quartic(x: float) -> float:
+    return lib().oracle_quartic(float(x))
+
+
+def quartic_cdf(y: float) -> float:
+    return lib().oracle_quartic_cdf(float(y))
+
+
+def freq_feature(x: float, d: int, enc_mode: int = ENC_CHEAP) -> float:
+    return lib().oracle_freq_feature(float(x), int(d), int(enc_mode))
+
+
+def oneblob(s: float, k: int = 4, enc_mode: int = ENC_CHEAP) -> np.ndarray:
+    out = np.zeros(k, dtype=np.float64)
+    lib().oracle_oneblob(float(s), int(k), int(enc_mode), _p(out))
+    return out
+
+
+# ------------------------------------------------------------------- steps
+def lcg_params(n_pool: int, frame_seed: int) -> tuple[int, int]:
+    a, c = ctypes.c_uint64(), ctypes.c_uint64()
+    lib().oracle_lcg_params(int(n_pool), int(frame_seed), ctypes.byref(a), ctypes.byref(c))
+    return a.value, c.value
+
+
+def permutation(n_pool: int, frame_seed: int) -> np.ndarray:
+    out = np.zeros(n_pool, dtype=np.int64)
+    lib().oracle_permutation(int(n_pool), int(frame_seed), _p(out))
+    return out
+
+
+def gather(pool, target, batch: int, frame_seed: int, step: int):
+    pool, target = _f32(pool), _f32(target)
+    rec = np.zeros((batch, 16), dtype=np.float32)
+    tgt = np.zeros((batch, 3), dtype=np.float32)
+    idx = np.zeros(batch, dtype=np.int64)
+    lib().oracle_gather(_p(pool), _p(target), pool.shape[0], int(batch), int(frame_seed), int(step), _p(rec),
+                        _p(tgt), _p(idx))
+    return rec, tgt, idx
+
+
+def encode(rec, enc_mode: int = ENC_CHEAP, pad_value: float = 1.0) -> np.ndarray:
+    rec = _f32(rec).reshape(-1, 16)
+    out = np.zeros((rec.shape[0], 64), dtype=np.float64)
+    lib().oracle_encode(_p(rec), rec.shape[0], int(enc_mode), float(pad_value), _p(out))
+    return out
+
+
+def forward(W, dims, x, keep_acts: bool = False):
+    W, x, d = _f64(W), _f64(x), _dims(dims)
+    n = x.shape[0]
+    L = len(dims) - 1
+    y = np.zeros((n, dims[-1]), dtype=np.float64)
+    acts = np.zeros(sum(n * dims[l] for l in range(L)), dtype=np.float64) if keep_acts else None
+    lib().oracle_forward(_p(W), _p(d), L, _p(x), n, _p(y), _p(acts))
+    return (y, acts) if keep_acts else y
+
+
+def loss(yhat, target, loss_mode: int = LOSS_LUMINANCE, eps: float = 0.01):
+    yhat, target = _f64(yhat), _f32(target)
+    g = np.zeros_like(yhat)
+    val = lib().oracle_loss(_p(yhat), _p(target), yhat.shape[0], int(loss_mode), float(eps), _p(g))
+    return val, g
+
+
+def backward(W, dims, acts, g) -> np.ndarray:
+    W, acts, g, d = _f64(W), _f64(acts), _f64(g), _dims(dims)
+    dW = np.zeros_like(W)
+    lib().oracle_backward(_p(W), _p(d), len(dims) - 1, _p(acts), _p(g), g.shape[0], _p(dW))
+    return dW
+
+
+def adam(W, m, v, g, t: int, lr=1e-2, b1=0.9, b2=0.99, eps=1e-8):
+    """Returns updated copies (W, m, v) after Adam step t (t >= 1)."""
+    W, m, v, g = _f64(W).copy(), _f64(m).copy(), _f64(v).copy(), _f64(g)
+    lib().oracle_adam(_p(W), _p(m), _p(v), _p(g), W.size, int(t), lr, b1, b2, eps)
+    return W, m, v
+
+
+def infer(W, dims, rec, enc_mode: int = ENC_CHEAP, pad_value: float = 1.0) -> np.ndarray:
+    W, d, rec = _f64(W), _dims(dims), _f32(rec).reshape(-1, 16)
+    y = np.zeros((rec.shape[0], dims[-1]), dtype=np.float64)
+    lib().oracle_infer(_p(W), _p(d), len(dims) - 1, _p(rec), rec.shape[0], int(enc_mode), float(pad_value), _p(y))
+    return y
+
+
+class TrainState:
+    """FP64 master weights, Adam moments and step counter of one cache."""
+
+    def __init__(self, W, dims):
+        self.dims = list(dims)
+        self.W = _f64(W).copy()
+        self.m = np.zeros_like(self.W)
+        self.v = np.zeros_like(self.W)
+        self.t = 0
+
+    def step(self, pool, target, batch: int, frame_seed: int, step: int, enc_mode=ENC_CHEAP, pad_value=1.0,
+             loss_mode=LOSS_LUMINANCE, loss_eps=0.01, lr=1e-2, b1=0.9, b2=0.99, adam_eps=1e-8,
+             want_grad: bool = False):
+        pool, target = _f32(pool), _f32(target)
+        t = ctypes.c_int64(self.t)
+        grad = np.zeros_like(self.W) if want_grad else None
+        val = lib().oracle_train_step(_p(self.W), _p(self.m), _p(self.v), ctypes.byref(t), _p(_dims(self.dims)),
+                                      len(self.dims) - 1, _p(pool), _p(target), pool.shape[0], int(batch),
+                                      int(frame_seed), int(step), int(enc_mode), float(pad_value), int(loss_mode),
+                                      float(loss_eps), lr, b1, b2, adam_eps, _p(grad))
+        self.t = t.value
+        return (val, grad) if want_grad else val
