@@ -1,0 +1,304 @@
+"""Benchmark of the neural radiance cache frame on GB300.
+
+One step = one 1080p frame of the cache's hot path (Sec. 3.1-3.5): the cache
+query for 1920 x 1080 = 2,073,600 path vertices, then 4 training steps of
+16,384 records each drawn (shuffled, disjoint) from the frame's 65,536-record
+pool, FP16 tensor-core products with FP32 accumulation and FP32 master weights
+and Adam state.  Inputs are seeded synthetic records shaped like the paper's
+workload (records U[0,1]^3 positions, directions and normals uniform on the
+sphere, roughness and albedos U[0,1]; targets from an analytic HDR field).
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle instead
+(a deliberately slow correctness reference, bounded sample per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_QUERIES = 1920 * 1080
+BATCH = 16384
+N_STEPS = 4
+N_POOL = BATCH * N_STEPS
+FLOP_QUERY = 2 * 20672          # forward pass, multiply-adds x 2
+FLOP_RECORD = 41344 + 33152 + 41344  # forward + backward data + weight gradients
+METRIC = "ms/frame and Mqueries/s (infer+train) fused vs plain FP32 path; % tensor peak; p99 frame ms"
+WORKLOAD = ("1080p frame: 2,073,600 cache queries + 4 train steps x 16,384 records from a 65,536-record pool; "
+            "width-64 5-hidden-layer MLP, 64-dim encoding (cheap primitives, pad 1)")
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d.get("bf16_tflops", 1900.0), d.get("bf16_tflops_sustained", 1700.0), d.get("hbm_gbs", 6800.0), "measured"
+    return 1900.0, 1700.0, 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        rows = [ln.split(",") for ln in self.out.strip().splitlines() if ln.count(",") >= 8]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip().lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_frame(budget_s: float, seed: int = 2106):
+    """Times the FP64 oracle on a bounded sample of the frame; returns (Mqueries/s, description, cores)."""
+    import numpy as np
+
+    from oracle import oracle as O
+    from paper_2106_12372_gb300 import synth
+
+    dims = synth.layer_dims()
+    w0 = synth.xavier_weights(dims, seed=seed)
+    O.lib()
+    nq = 8192
+    rec = synth.make_records(nq, seed=seed + 1)
+    t0 = time.perf_counter()
+    O.infer(w0, dims, rec)
+    t_q = (time.perf_counter() - t0) / nq
+    # size the sample to the budget: queries take ~60 % of it, one train batch the rest
+    nq = int(min(N_QUERIES, max(8192, 0.6 * budget_s / max(t_q, 1e-9))))
+    rec = synth.make_records(nq, seed=seed + 2)
+    t0 = time.perf_counter()
+    O.infer(w0, dims, rec)
+    t_inf = time.perf_counter() - t0
+    pool, tgt = synth.make_training_pool(N_POOL, seed=seed + 3)
+    st = O.TrainState(w0, dims)
+    nb = BATCH
+    t0 = time.perf_counter()
+    st.step(pool, tgt, nb, synth.frame_seed(seed, 0), 0)
+    t_tr = time.perf_counter() - t0
+    frame_s = t_inf * (N_QUERIES / nq) + t_tr * N_STEPS * (BATCH / nb)
+    cores = int(os.environ.get("ORACLE_THREADS", os.cpu_count() or 1))
+    desc = (f"{nq} queries + 1 train step of {nb} records timed, scaled to the frame "
+            f"({N_QUERIES} queries + {N_STEPS} steps); oracle wall {t_inf + t_tr:.1f} s")
+    return N_QUERIES / frame_s / 1e6, desc, cores, frame_s * 1e3
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    values = []
+    descs = []
+    cores = 1
+    per = max(3.0, 60.0 / max(1, args.steps + args.warmup))
+    for i in range(args.warmup + args.steps):
+        v, d, cores, _ = cpu_oracle_frame(per)
+        if i >= args.warmup:
+            values.append(v)
+            descs.append(d)
+    v = statistics.median(values)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mqueries/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": N_QUERIES / (v * 1e6) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": v, "unit": "Mqueries/s", "cores": cores, "kind": "oracle", "sample": descs[-1]},
+            "e2e": {"value": v, "unit": "Mqueries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_2106_12372_gb300 import nrc, synth
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2106_12372_gb300 import build
+
+    build.build()
+    stream = torch.cuda.current_stream()
+
+    seed = 2106 + rank
+    queries = [torch.from_numpy(synth.make_records(N_QUERIES, seed=seed + k)).to(dev) for k in range(2)]
+    pool_np, tgt_np = synth.make_training_pool(N_POOL, seed=seed)
+    pool, tgt = torch.from_numpy(pool_np).to(dev), torch.from_numpy(tgt_np).to(dev)
+    rgb = torch.empty((N_QUERIES, 3), device=dev)
+    losses = torch.zeros(N_STEPS, device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # 256 MB > 129 MB L2
+
+    cache = nrc.Cache(dtype=args.dtype, seed=seed)
+
+    def frame(k, ev=None):
+        q = queries[k % 2]
+        if ev:
+            ev[0].record(stream)
+        cache.infer(q, rgb)
+        if ev:
+            ev[1].record(stream)
+        for s in range(N_STEPS):
+            cache.train_step(pool, tgt, BATCH, synth.frame_seed(seed, k), s, loss_out=losses[s:s + 1])
+        if ev:
+            ev[2].record(stream)
+
+    for k in range(args.warmup):
+        frame(k)
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    launches0 = cache.launches
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            frame(args.warmup + k, evs[k])
+        torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    launches = cache.launches - launches0
+    cache.check_error()
+    frame_ms = [e[0].elapsed_time(e[2]) for e in evs]
+    infer_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    train_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    total_ms = sum(frame_ms)
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = t.item()
+    value = N_QUERIES * args.steps * ws / (total_ms / 1e3) / 1e6
+
+    # plain per-layer FP32 path on the same frame (a few frames; same cache shape)
+    plain = nrc.Cache(dtype="fp32", path=nrc.PATH_PLAIN, seed=seed)
+    pev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    plain_ms = []
+    for k in range(3):
+        flush.zero_()
+        pev[0].record(stream)
+        plain.infer(queries[0], rgb)
+        for s in range(N_STEPS):
+            plain.train_step(pool, tgt, BATCH, synth.frame_seed(seed, k), s)
+        pev[1].record(stream)
+        torch.cuda.synchronize()
+        if k > 0:
+            plain_ms.append(pev[0].elapsed_time(pev[1]))
+    plain.close()
+
+    # end to end: host (pinned) buffers through nrc_frame_host, copies inside the timed region
+    qh = torch.from_numpy(synth.make_records(N_QUERIES, seed=seed + 7)).pin_memory()
+    ph, th = pool.cpu().pin_memory(), tgt.cpu().pin_memory()
+    rgb_h = torch.empty((N_QUERIES, 3)).pin_memory()
+    loss_h = torch.zeros(N_STEPS).pin_memory()
+    for k in range(2):
+        cache.frame_host(qh, rgb_h, ph, th, BATCH, N_STEPS, synth.frame_seed(seed, k), loss_out=loss_h)
+    e2e_n = max(3, min(args.steps, 10))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(e2e_n):
+        cache.frame_host(qh, rgb_h, ph, th, BATCH, N_STEPS, synth.frame_seed(seed, k), loss_out=loss_h)
+    e2e_s = (time.perf_counter() - t0) / e2e_n
+    h2d = N_QUERIES * 64 + N_POOL * 64 + N_POOL * 12
+    d2h = N_QUERIES * 12 + N_STEPS * 4
+
+    if rank != 0:
+        return
+    burst, sustained, hbm, src = peaks()
+    inf_med = statistics.median(infer_ms)
+    achieved = FLOP_QUERY * N_QUERIES / (inf_med / 1e3) / 1e12
+    frame_flop = FLOP_QUERY * N_QUERIES + FLOP_RECORD * BATCH * N_STEPS
+    med = statistics.median(frame_ms)
+    p99 = float(np.percentile(frame_ms, 99))
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        v, d, cores, _ = cpu_oracle_frame(args.cpu_budget)
+        cpu = {"value": v, "unit": "Mqueries/s", "cores": cores, "kind": "oracle", "sample": d}
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mqueries/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+        "config": {"workload": WORKLOAD, "queries": N_QUERIES, "train_steps": N_STEPS, "batch": BATCH,
+                   "pool": N_POOL, "l2": "flushed (256 MB write) between frames, outside the events",
+                   "parallelism": f"replicas x{ws}"},
+        "frame_ms_median": med, "frame_ms_p99": p99, "infer_ms_median": inf_med,
+        "train_ms_median": statistics.median(train_ms),
+        "frame_tflops": frame_flop / (med / 1e3) / 1e12, "frame_frac_of_peak": frame_flop / (med / 1e3) / 1e12 / burst,
+        "plain_fp32_ms_per_frame": statistics.median(plain_ms) if plain_ms else None,
+        "roofline": {"kernel": "k_infer_tc (fused encode + 6 tcgen05 layers)", "bound": "tensor", "achieved": achieved,
+                     "peak": burst, "unit": "TFLOP/s", "frac": achieved / burst, "traffic": None,
+                     "peak_source": f"{src} bf16 dense burst (fp16 peak = bf16 peak)"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": N_QUERIES / e2e_s / 1e6, "unit": "Mqueries/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "paper_context": "RTX 3090, half: query 1.59 ms + training 1.11 ms per 1080p frame (Table 3)",
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="nrc", choices=["nrc", "reference"])
+    ap.add_argument("--dtype", default="fp16", choices=["fp16", "bf16", "fp32"])
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

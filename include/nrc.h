@@ -1,0 +1,203 @@
+/*
+ * nrc.h - C ABI of the GB300 (sm_103a) neural radiance cache hot path.
+ *
+ * The library computes the per-frame work of a neural radiance cache
+ * (Mueller et al., "Real-time Neural Radiance Caching for Path Tracing",
+ * ACM TOG 40(4) 2021): inference of the cached scattered radiance for every
+ * path vertex that queries the cache (Sec. 3.1), and online training on the
+ * frame's training records (Sec. 3.3, 3.5) with the relative L2 loss (Eq. 5)
+ * and Adam (Sec. 5).  The network is the bias-free ReLU MLP of Sec. 5
+ * ("Architecture"): 64 encoded inputs (Table 1, Sec. 3.6), 5 hidden layers of
+ * width 64, 3 linear RGB outputs.
+ *
+ * Conventions (all entry points):
+ *  - Every call returns an nrc_status.  NRC_OK is 0.  On failure the
+ *    thread-local string from nrc_last_error_string() says why.  No call
+ *    aborts or prints.
+ *  - Work is asynchronous on the caller's stream (an nrc_stream is a
+ *    cudaStream_t; NULL means the legacy default stream).  Only
+ *    nrc_get_state, nrc_set_state, nrc_check_error, nrc_frame_host and
+ *    nrc_destroy synchronise that stream.
+ *  - The CALLER owns every buffer passed in; the library reads and writes it
+ *    only during the stream-ordered execution of the call.  Device pointers
+ *    must be device-accessible memory of the current device; record and
+ *    output pointers must be 16-byte aligned.
+ *  - The LIBRARY owns the cache state created by nrc_create: FP32 master
+ *    weights, Adam moments, the step counter, the low-precision weight image
+ *    the tensor-core kernels stage into shared memory, scratch for weight
+ *    gradient partials, and a device error word.
+ *  - Errors: a NULL cache or NULL pointer with n > 0, n < 0, a misaligned
+ *    pointer or an out-of-range enum give NRC_ERR_INVALID_ARG and launch
+ *    nothing.  n == 0 is a no-op that returns NRC_OK.  A CUDA error gives
+ *    NRC_ERR_CUDA; an allocation failure NRC_ERR_OOM; a device-side bounded
+ *    wait that gave up sets the error word, reported as NRC_ERR_TIMEOUT by
+ *    nrc_check_error.
+ *
+ * Record layout (query and training records, 16 x float32 = 64 bytes, AoS):
+ *    [x0, x1, x2, u_w, v_w, u_n, v_n, r, a0, a1, a2, b0, b1, b2, pad, pad]
+ *  x: position in [0,1]^3 (scene-normalised); (u_w, v_w) and (u_n, v_n):
+ *  scattered direction and surface normal as spherical coordinates
+ *  normalised to [0,1]^2, u = theta/pi, v = phi/(2 pi) (Table 1's sph());
+ *  r: roughness; a, b: diffuse and specular reflectance.  Targets are
+ *  float32 [n][3] RGB radiance.
+ */
+#ifndef NRC_H_
+#define NRC_H_
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define NRC_API __attribute__((visibility("default")))
+#else
+#define NRC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* nrc_stream; /* identical to cudaStream_t */
+
+typedef enum nrc_status {
+  NRC_OK = 0,
+  NRC_ERR_INVALID_ARG = 1,
+  NRC_ERR_CUDA = 2,
+  NRC_ERR_OOM = 3,
+  NRC_ERR_TIMEOUT = 4,
+  NRC_ERR_UNSUPPORTED = 5
+} nrc_status;
+
+/* Arithmetic type of the MLP's matrix products.  NRC_FP32: FP32 SIMT FMA
+ * (the parity path).  NRC_FP16 / NRC_BF16: tcgen05 tensor-core products with
+ * FP32 accumulation; master weights, Adam moments and the loss stay FP32. */
+enum { NRC_FP32 = 0, NRC_FP16 = 1, NRC_BF16 = 2 };
+
+/* Encoding primitives (Sec. 5, Fig. 7): CHEAP replaces the sine by the
+ * triangle wave tri(x) = 2|x mod 2 - 1| - 1 and the one-blob Gaussian by the
+ * quartic 15/16 (1 - x^2)^2; EXACT keeps sine and Gaussian. */
+enum { NRC_ENC_CHEAP = 0, NRC_ENC_EXACT = 1 };
+
+/* Normalisation of the relative L2 loss (Eq. 5): LUMINANCE divides every
+ * channel by the squared luminance (Rec. 709 weights) of the prediction;
+ * PER_CHANNEL divides each channel by its own squared prediction. */
+enum { NRC_LOSS_LUMINANCE = 0, NRC_LOSS_PER_CHANNEL = 1 };
+
+/* Execution path.  FUSED: one fused kernel per stage (encoding fused into the
+ * first layer, activations on chip).  PLAIN: a separate FP32 kernel per layer
+ * with every activation round-tripping through HBM (a reference point). */
+enum { NRC_PATH_FUSED = 0, NRC_PATH_PLAIN = 1 };
+
+typedef struct nrc_config {
+  int32_t width;         /* hidden width; 64 */
+  int32_t hidden_layers; /* number of hidden layers; 5 (1..8) */
+  int32_t dtype;         /* NRC_FP32 | NRC_FP16 | NRC_BF16 */
+  int32_t enc_mode;      /* NRC_ENC_CHEAP | NRC_ENC_EXACT */
+  int32_t loss_mode;     /* NRC_LOSS_LUMINANCE | NRC_LOSS_PER_CHANNEL */
+  int32_t path;          /* NRC_PATH_FUSED | NRC_PATH_PLAIN */
+  float pad_value;       /* value of the 2 padding inputs; 1.0 (Sec. 3.6) */
+  float lr;              /* Adam learning rate; 1e-2 */
+  float beta1, beta2;    /* Adam decay rates; 0.9, 0.99 */
+  float adam_eps;        /* Adam epsilon; 1e-8 */
+  float loss_eps;        /* epsilon of Eq. 5; 0.01 */
+  uint64_t seed;         /* seed of the Xavier-uniform initial weights */
+} nrc_config;
+
+typedef struct nrc_cache nrc_cache;
+
+/* Fills *cfg with the defaults listed above. */
+NRC_API void nrc_default_config(nrc_config* cfg);
+
+/* Creates a cache: allocates its state on the current device and draws
+ * Xavier-uniform weights U(+-sqrt(6/(fan_in+fan_out))) from SplitMix64(seed)
+ * (weights layer after layer, row-major [out][in], FP64 then rounded to
+ * FP32); Adam moments and the step counter start at zero.  The weight upload
+ * is ordered on `stream`.  *out receives the handle.  Returns
+ * NRC_ERR_UNSUPPORTED for widths other than 64 or a dtype the device lacks. */
+NRC_API nrc_status nrc_create(const nrc_config* cfg, nrc_stream stream, nrc_cache** out);
+
+/* Frees the cache after synchronising its internal work.  NULL is a no-op. */
+NRC_API nrc_status nrc_destroy(nrc_cache* cache);
+
+/* Number of weights (FP32 elements of nrc_get_state's `weights`). */
+NRC_API int64_t nrc_param_count(const nrc_cache* cache);
+
+/* Input encoding (Sec. 3.6, Table 1): records[n][16] (device) ->
+ * out[n][64] (device) in out_dtype (NRC_FP32 | NRC_FP16 | NRC_BF16).
+ * Features: 12 frequency features of each position axis (axis-major, sine or
+ * triangle wave of 2^d * pi * x, d = 0..11), one-blob k = 4 of u_w, v_w,
+ * u_n, v_n and of 1 - exp(-r), the six albedos, two pad entries. */
+NRC_API nrc_status nrc_encode(nrc_cache* cache, const float* records, int64_t n, void* out, int32_t out_dtype,
+                      nrc_stream stream);
+
+/* Cache query (Sec. 3.1; Sec. 4 fully fused network): rgb[n][3] (device) =
+ * MLP(encode(records[n][16])) with the current weights. */
+NRC_API nrc_status nrc_infer(nrc_cache* cache, const float* records, int64_t n, float* rgb, nrc_stream stream);
+
+/* Training-record shuffle and batch gather (Sec. 3.5): for j < batch,
+ * rec_out[j] = pool[perm(step * batch + j)] and tgt_out[j] = target[same],
+ * perm(i) = (a*i + c) mod n_pool with a, c drawn from SplitMix64(frame_seed)
+ * (a = 1 + 4 (h mod floor(n_pool/4)) raised by 2 until gcd(a, n_pool) = 1,
+ * c = h' mod n_pool).  Requires (step+1)*batch <= n_pool < 2^31.  All
+ * pointers are device pointers; tgt_out may be NULL (target then unused). */
+NRC_API nrc_status nrc_gather(const float* pool, const float* target, int64_t n_pool, int64_t batch, uint64_t frame_seed,
+                      int32_t step, float* rec_out, float* tgt_out, nrc_stream stream);
+
+/* One optimisation step (Sec. 3.3: several per frame, each on a disjoint
+ * slice of the shuffled records): gather batch `step_in_frame` of the frame's
+ * pool (as nrc_gather), encode, forward, relative L2 loss (Eq. 5) averaged
+ * over the 3*batch terms, backward pass, then Adam on the FP32 master weights
+ * (step counter t incremented first).  pool[n_pool][16], target[n_pool][3]
+ * are device pointers; loss_out (device, 1 float, may be NULL) receives the
+ * batch's loss before the update.  Requires (step_in_frame+1)*batch <=
+ * n_pool and batch <= 1048576. */
+NRC_API nrc_status nrc_train_step(nrc_cache* cache, const float* pool, const float* target, int64_t n_pool, int64_t batch,
+                          uint64_t frame_seed, int32_t step_in_frame, float* loss_out, nrc_stream stream);
+
+/* One frame (Sec. 3.1-3.5): the cache query rgb = infer(queries) with the
+ * weights before this frame's training, then n_steps train steps on the
+ * pool (steps 0 .. n_steps-1 of frame_seed's shuffle).  loss_out (device,
+ * n_steps floats, may be NULL) receives each step's loss.  Device pointers. */
+NRC_API nrc_status nrc_frame(nrc_cache* cache, const float* queries, int64_t n_queries, float* rgb, const float* pool,
+                     const float* target, int64_t n_pool, int64_t batch, int32_t n_steps, uint64_t frame_seed,
+                     float* loss_out, nrc_stream stream);
+
+/* nrc_frame with HOST buffers: copies queries, pool and target host->device
+ * into library-owned staging buffers (grown on demand), runs the frame, and
+ * copies rgb[n_queries][3] and the n_steps losses (loss_out, host, may be
+ * NULL) back.  Synchronises `stream` before returning.  Pinned host memory
+ * gives asynchronous copies. */
+NRC_API nrc_status nrc_frame_host(nrc_cache* cache, const float* queries, int64_t n_queries, float* rgb, const float* pool,
+                          const float* target, int64_t n_pool, int64_t batch, int32_t n_steps, uint64_t frame_seed,
+                          float* loss_out, nrc_stream stream);
+
+/* Copies the state out (host pointers, each nrc_param_count floats; any may
+ * be NULL): FP32 weights layer after layer, row-major [out][in]; Adam first
+ * and second moments in the same layout; *step = Adam step counter.
+ * Synchronises `stream`. */
+NRC_API nrc_status nrc_get_state(nrc_cache* cache, float* weights, float* adam_m, float* adam_v, int64_t* step,
+                         nrc_stream stream);
+
+/* Replaces the state (host pointers as in nrc_get_state; NULL moments are
+ * zeroed; weights must not be NULL) and rebuilds the low-precision weight
+ * image.  Synchronises `stream`. */
+NRC_API nrc_status nrc_set_state(nrc_cache* cache, const float* weights, const float* adam_m, const float* adam_v,
+                         int64_t step, nrc_stream stream);
+
+/* Selects NRC_PATH_FUSED or NRC_PATH_PLAIN for later calls. */
+NRC_API nrc_status nrc_set_path(nrc_cache* cache, int32_t path);
+
+/* Synchronises `stream`, then reads and clears the device error word:
+ * NRC_ERR_TIMEOUT if a bounded device wait gave up since the last check. */
+NRC_API nrc_status nrc_check_error(nrc_cache* cache, nrc_stream stream);
+
+/* Number of kernels the library launched on this cache since creation. */
+NRC_API int64_t nrc_launch_count(const nrc_cache* cache);
+
+/* Why the last failing call on this thread failed ("" if none). */
+NRC_API const char* nrc_last_error_string(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NRC_H_ */

@@ -1,0 +1,184 @@
+// Internal declarations of the GB300 neural radiance cache library.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/nrc.h"
+
+namespace nrc {
+
+constexpr int kRecFloats = 16;  // 64-byte record
+constexpr int kEncDims = 64;    // Table 1: 62 features + 2 pad (Sec. 3.6)
+constexpr int kOutDims = 3;     // RGB
+constexpr int kMaxMats = 9;     // hidden layers <= 8
+constexpr int kTile = 128;      // batch rows per tensor-core tile (MMA M)
+constexpr int kOutPad = 16;     // output layer padded to N = 16 for the MMA
+constexpr int kMaxBatch = 1 << 16;  // training records per step
+
+// Device error word bits.
+constexpr int kErrTimeout = 1;
+// Bounded device waits give up after this many nanoseconds.
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;
+
+struct NetShape {
+  int n_mats;              // hidden_layers + 1
+  int dims[kMaxMats + 1];  // d_0 = 64, d_1..d_H = width, d_L = 3
+  int w_off[kMaxMats + 1]; // FP32 element offset of matrix l (row-major [out][in])
+  int n_params;
+};
+
+// Byte layout of the 16-bit weight image for the tensor-core kernels: matrix
+// l is stored as N_l = round_up(d_{l+1}, 16) rows of K_l = d_l elements,
+// K-major with the 128-byte swizzle (8-row atoms of 1024 bytes; 16-byte chunk
+// c of row n stored at chunk c ^ (n % 8)), so that one bulk copy puts it in
+// shared memory exactly as the tcgen05 descriptors read it.  Only K = 64 is
+// supported (one 128-byte swizzle row per matrix row).
+struct ImageShape {
+  int off[kMaxMats + 1];  // byte offset of matrix l; off[n_mats] = total bytes
+  int rows[kMaxMats];     // N_l
+};
+
+struct Cache {
+  nrc_config cfg;
+  NetShape net;
+  ImageShape img;
+  float* w = nullptr;     // FP32 master weights [n_params]
+  float* m = nullptr;     // Adam first moment
+  float* v = nullptr;     // Adam second moment
+  long long* t = nullptr; // Adam step counter (device)
+  uint8_t* wimg = nullptr;        // 16-bit weight image (tensor-core path)
+  float* partials = nullptr;      // [max_partials][n_params + 1] weight-gradient + loss partials
+  int max_partials = 0;
+  int* err = nullptr;     // device error word
+  // plain-path scratch (grown on demand)
+  float* plain_buf = nullptr;
+  size_t plain_bytes = 0;
+  // nrc_frame_host staging (grown on demand)
+  void* stage = nullptr;
+  size_t stage_bytes = 0;
+  long long launches = 0;
+  int sm_count = 0;
+  int device = 0;
+};
+
+// ---------------------------------------------------------------- host side
+void set_error(const char* fmt, ...);
+nrc_status cuda_status(cudaError_t e, const char* what);
+
+void make_net_shape(const nrc_config& cfg, NetShape* s);
+void make_image_shape(const NetShape& s, ImageShape* img);
+
+// Shuffle parameters (Sec. 3.5): perm(i) = (a*i + c) mod n_pool.
+void lcg_params(int64_t n_pool, uint64_t frame_seed, uint64_t* a, uint64_t* c);
+
+// Kernel launchers (each returns the launch's cudaError_t).
+// Grows the weight-gradient partial buffer to at least `count` partials.
+cudaError_t ensure_partials(Cache* c, int count);
+
+cudaError_t launch_gather(const float* pool, const float* target, int64_t n_pool, int64_t batch, uint64_t a,
+                          uint64_t c, int step, float* rec_out, float* tgt_out, cudaStream_t st);
+cudaError_t launch_encode(const float* rec, int64_t n, void* out, int out_dtype, int enc_mode, float pad,
+                          cudaStream_t st);
+cudaError_t launch_infer_simt(Cache* c, const float* rec, int64_t n, float* rgb, cudaStream_t st);
+cudaError_t launch_train_simt(Cache* c, const float* pool, const float* target, int64_t n_pool, int64_t batch,
+                              uint64_t a, uint64_t cc, int step, int* n_partials, cudaStream_t st);
+cudaError_t launch_adam(Cache* c, int n_partials, float grad_scale, float* loss_out, cudaStream_t st);
+cudaError_t launch_build_image(Cache* c, cudaStream_t st);
+cudaError_t launch_step_increment(Cache* c, cudaStream_t st);
+cudaError_t launch_infer_tc(Cache* c, const float* rec, int64_t n, float* rgb, cudaStream_t st);
+cudaError_t launch_train_tc(Cache* c, const float* pool, const float* target, int64_t n_pool, int64_t batch,
+                            uint64_t a, uint64_t cc, int step, int* n_partials, float* grad_scale, cudaStream_t st);
+// Plain per-layer FP32 path.
+cudaError_t plain_infer(Cache* c, const float* rec, int64_t n, float* rgb, cudaStream_t st);
+cudaError_t plain_train(Cache* c, const float* pool, const float* target, int64_t n_pool, int64_t batch,
+                        uint64_t a, uint64_t cc, int step, float* loss_out, cudaStream_t st);
+
+// ------------------------------------------------------------- device side
+// Input encoding of one record (Sec. 3.6, Table 1; Sec. 5 cheap primitives).
+// Writes the 64 features in order: x0 d=0..11, x1, x2 (frequency), one-blob
+// of u_w, v_w, u_n, v_n, 1-exp(-r) (4 bins each), a0..a2, b0..b2, pad, pad.
+
+// Triangle wave standing in for sin(pi*y) (Fig. 7): tri(y - 1/2) with
+// tri(t) = 2|t mod 2 - 1| - 1, evaluated as |4 frac(y/2 - 1/4) - 2| - 1.
+// For y = 2^d x with x in [0, 1] the only rounding is in y/2 - 1/4 (at most
+// 2^-25), i.e. at most ~1.2e-7 in the result.
+__device__ __forceinline__ float tri_sin(float y) {
+  const float t = fmaf(y, 0.5f, -0.25f);
+  const float f = t - floorf(t);
+  return fabsf(fmaf(4.0f, f, -2.0f)) - 1.0f;
+}
+
+// Clamped antiderivative of the quartic kernel 15/16 (1 - y^2)^2:
+// Q(y) = 15/16 y (1 - 2/3 y^2 + 1/5 y^4) on [-1, 1], +-1/2 outside.
+__device__ __forceinline__ float quartic_cdf(float y) {
+  y = fminf(1.0f, fmaxf(-1.0f, y));
+  const float y2 = y * y;
+  return y * fmaf(y2, fmaf(y2, 0.1875f, -0.625f), 0.9375f);
+}
+
+// Twice the mass of a standard Gaussian between 0 and y (bins are scaled by k).
+__device__ __forceinline__ float gauss_cdf2(float y) { return erff(y * 0.70710678118654752f); }
+
+template <int MODE>
+__device__ __forceinline__ void oneblob4(float s, float* out) {
+  // Bin i of k = 4 holds the kernel mass over [i/4, (i+1)/4]; kernel width 1/4.
+  const float ks = 4.0f * s;
+  float prev = (MODE == 0) ? quartic_cdf(-ks) : gauss_cdf2(-ks);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float hi = float(i + 1) - ks;
+    const float cur = (MODE == 0) ? quartic_cdf(hi) : gauss_cdf2(hi);
+    out[i] = (MODE == 0) ? cur - prev : 0.5f * (cur - prev);
+    prev = cur;
+  }
+}
+
+template <int MODE>
+__device__ __forceinline__ void encode_record(const float* r, float pad, float* f) {
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+#pragma unroll
+    for (int d = 0; d < 12; ++d) {
+      const float y = r[j] * float(1 << d);  // exact
+      f[12 * j + d] = (MODE == 0) ? tri_sin(y) : sinpif(y);
+    }
+  }
+  oneblob4<MODE>(r[3], f + 36);
+  oneblob4<MODE>(r[4], f + 40);
+  oneblob4<MODE>(r[5], f + 44);
+  oneblob4<MODE>(r[6], f + 48);
+  oneblob4<MODE>(-expm1f(-r[7]), f + 52);
+#pragma unroll
+  for (int j = 0; j < 6; ++j) f[56 + j] = r[8 + j];
+  f[62] = pad;
+  f[63] = pad;
+}
+
+__device__ __forceinline__ void load_record(const float* rec, int64_t row, float* r) {
+  const float4* p = reinterpret_cast<const float4*>(rec + row * kRecFloats);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float4 v = __ldg(p + q);
+    r[4 * q + 0] = v.x;
+    r[4 * q + 1] = v.y;
+    r[4 * q + 2] = v.z;
+    r[4 * q + 3] = v.w;
+  }
+}
+
+// Byte offset of element (n, k) of a 16-bit K-major matrix with 128-byte rows
+// in the 128-byte-swizzled layout.
+__host__ __device__ __forceinline__ uint32_t sw128_offset(uint32_t n, uint32_t k) {
+  return (n >> 3) * 1024u + (n & 7u) * 128u + ((((k >> 3) ^ n) & 7u) << 4) + (k & 7u) * 2u;
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+}  // namespace nrc

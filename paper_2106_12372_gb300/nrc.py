@@ -1,0 +1,227 @@
+"""Thin Python binding of the C ABI in ``include/nrc.h`` (argument marshalling only).
+
+Every step of the hot path runs in the CUDA library ``libnrc.so``; this module
+passes tensor data pointers, sizes and the current CUDA stream through ctypes.
+PyTorch is used for device memory and streams only.  There is no fallback: if
+the library is missing, :func:`lib` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnrc.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "nrc.h")
+
+NRC_OK, NRC_ERR_INVALID_ARG, NRC_ERR_CUDA, NRC_ERR_OOM, NRC_ERR_TIMEOUT, NRC_ERR_UNSUPPORTED = range(6)
+FP32, FP16, BF16 = 0, 1, 2
+ENC_CHEAP, ENC_EXACT = 0, 1
+LOSS_LUMINANCE, LOSS_PER_CHANNEL = 0, 1
+PATH_FUSED, PATH_PLAIN = 0, 1
+DTYPES = {"fp32": FP32, "fp16": FP16, "bf16": BF16}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class NrcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"nrc status {status}: {msg}")
+        self.status = status
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("width", ctypes.c_int32),
+        ("hidden_layers", ctypes.c_int32),
+        ("dtype", ctypes.c_int32),
+        ("enc_mode", ctypes.c_int32),
+        ("loss_mode", ctypes.c_int32),
+        ("path", ctypes.c_int32),
+        ("pad_value", ctypes.c_float),
+        ("lr", ctypes.c_float),
+        ("beta1", ctypes.c_float),
+        ("beta2", ctypes.c_float),
+        ("adam_eps", ctypes.c_float),
+        ("loss_eps", ctypes.c_float),
+        ("seed", ctypes.c_uint64),
+    ]
+
+
+def declared_functions() -> list[str]:
+    """Names of the entry points declared in include/nrc.h."""
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^NRC_API [^(]*?\b(nrc_\w+)\(", text, flags=re.M)))
+
+
+def lib() -> ctypes.CDLL:
+    """Loads libnrc.so (built by ``__graft_entry__.build()``); raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        P, i64, i32, u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64
+        sig = {
+            "nrc_default_config": (None, [P]),
+            "nrc_create": (i32, [P, P, P]),
+            "nrc_destroy": (i32, [P]),
+            "nrc_param_count": (i64, [P]),
+            "nrc_encode": (i32, [P, P, i64, P, i32, P]),
+            "nrc_infer": (i32, [P, P, i64, P, P]),
+            "nrc_gather": (i32, [P, P, i64, i64, u64, i32, P, P, P]),
+            "nrc_train_step": (i32, [P, P, P, i64, i64, u64, i32, P, P]),
+            "nrc_frame": (i32, [P, P, i64, P, P, P, i64, i64, i32, u64, P, P]),
+            "nrc_frame_host": (i32, [P, P, i64, P, P, P, i64, i64, i32, u64, P, P]),
+            "nrc_get_state": (i32, [P, P, P, P, P, P]),
+            "nrc_set_state": (i32, [P, P, P, P, i64, P]),
+            "nrc_set_path": (i32, [P, i32]),
+            "nrc_check_error": (i32, [P, P]),
+            "nrc_launch_count": (i64, [P]),
+            "nrc_last_error_string": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+        return L
+
+
+def _check(status: int) -> None:
+    if status != NRC_OK:
+        msg = lib().nrc_last_error_string()
+        raise NrcError(status, msg.decode() if msg else "")
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def default_config(**kw) -> Config:
+    cfg = Config()
+    lib().nrc_default_config(ctypes.byref(cfg))
+    for k, v in kw.items():
+        if k == "dtype" and isinstance(v, str):
+            v = DTYPES[v]
+        setattr(cfg, k, v)
+    return cfg
+
+
+def gather(pool, target, batch: int, frame_seed: int, step: int, stream=None):
+    """Device gather of training batch ``step`` (Sec. 3.5): returns (records, targets)."""
+    import torch
+
+    rec = torch.empty((batch, 16), dtype=torch.float32, device=pool.device)
+    tgt = torch.empty((batch, 3), dtype=torch.float32, device=pool.device)
+    _check(lib().nrc_gather(_ptr(pool), _ptr(target), pool.shape[0], batch, frame_seed & (2**64 - 1), step,
+                            _ptr(rec), _ptr(tgt), _stream(stream)))
+    return rec, tgt
+
+
+class Cache:
+    """One neural radiance cache (weights, Adam state) owned by the CUDA library."""
+
+    def __init__(self, stream=None, **cfg_kw):
+        self.cfg = default_config(**cfg_kw)
+        h = ctypes.c_void_p()
+        _check(lib().nrc_create(ctypes.byref(self.cfg), _stream(stream), ctypes.byref(h)))
+        self._h = h
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().nrc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def n_params(self) -> int:
+        return lib().nrc_param_count(self._h)
+
+    @property
+    def launches(self) -> int:
+        return lib().nrc_launch_count(self._h)
+
+    def set_path(self, path: int) -> None:
+        _check(lib().nrc_set_path(self._h, path))
+
+    def encode(self, rec, out_dtype: str = "fp32", stream=None):
+        import torch
+
+        tdt = {"fp32": torch.float32, "fp16": torch.float16, "bf16": torch.bfloat16}[out_dtype]
+        out = torch.empty((rec.shape[0], 64), dtype=tdt, device=rec.device)
+        _check(lib().nrc_encode(self._h, _ptr(rec), rec.shape[0], _ptr(out), DTYPES[out_dtype], _stream(stream)))
+        return out
+
+    def infer(self, rec, out=None, stream=None):
+        import torch
+
+        if out is None:
+            out = torch.empty((rec.shape[0], 3), dtype=torch.float32, device=rec.device)
+        _check(lib().nrc_infer(self._h, _ptr(rec), rec.shape[0], _ptr(out), _stream(stream)))
+        return out
+
+    def train_step(self, pool, target, batch: int, frame_seed: int, step: int, loss_out=None, stream=None):
+        _check(lib().nrc_train_step(self._h, _ptr(pool), _ptr(target), pool.shape[0], batch,
+                                    frame_seed & (2**64 - 1), step, _ptr(loss_out), _stream(stream)))
+
+    def frame(self, queries, rgb, pool, target, batch: int, n_steps: int, frame_seed: int, loss_out=None,
+              stream=None):
+        _check(lib().nrc_frame(self._h, _ptr(queries), queries.shape[0], _ptr(rgb), _ptr(pool), _ptr(target),
+                               pool.shape[0], batch, n_steps, frame_seed & (2**64 - 1), _ptr(loss_out),
+                               _stream(stream)))
+
+    def frame_host(self, queries, rgb, pool, target, batch: int, n_steps: int, frame_seed: int, loss_out=None,
+                   stream=None):
+        """As :meth:`frame` with host (ideally pinned) tensors; copies are inside the call."""
+        _check(lib().nrc_frame_host(self._h, _ptr(queries), queries.shape[0], _ptr(rgb), _ptr(pool), _ptr(target),
+                                    pool.shape[0], batch, n_steps, frame_seed & (2**64 - 1), _ptr(loss_out),
+                                    _stream(stream)))
+
+    def get_state(self, stream=None):
+        n = self.n_params
+        w, m, v = (np.zeros(n, dtype=np.float32) for _ in range(3))
+        t = ctypes.c_int64()
+        _check(lib().nrc_get_state(self._h, w.ctypes.data, m.ctypes.data, v.ctypes.data, ctypes.byref(t),
+                                   _stream(stream)))
+        return w, m, v, t.value
+
+    def set_state(self, w, m=None, v=None, step: int = 0, stream=None):
+        n = self.n_params
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        assert w.size == n
+        m = None if m is None else np.ascontiguousarray(m, dtype=np.float32)
+        v = None if v is None else np.ascontiguousarray(v, dtype=np.float32)
+        _check(lib().nrc_set_state(self._h, w.ctypes.data, None if m is None else m.ctypes.data,
+                                   None if v is None else v.ctypes.data, step, _stream(stream)))
+
+    def check_error(self, stream=None) -> None:
+        _check(lib().nrc_check_error(self._h, _stream(stream)))
