@@ -191,13 +191,351 @@ cudaError_t launch_infer_tc(Cache* c, const float* rec, int64_t n, float* rgb, c
   return cudaGetLastError();
 }
 
-// Training for the 16-bit caches.  Until the tensor-core training kernel is
-// in place the FP32 fused kernel computes the gradient from the master
-// weights; Adam then refreshes the 16-bit image.
+// ------------------------------------------------------------- training
+// Fused training step on the tensor cores (Sec. 4, training the fully fused
+// network; Eq. 5; the weight-gradient contraction the paper leaves to a
+// split-k GEMM).  One warpgroup per CTA, one 128-row batch tile at a time;
+// each thread owns one gathered record (Sec. 3.5 shuffle).
+//  forward : H_{l+1} = ReLU(W_l H_l) as in inference; every H_l is also kept
+//            in shared memory (16-bit, 128-byte swizzled rows) for the
+//            weight gradients, and the sign masks [Z_l > 0] stay in registers;
+//  loss    : relative L2 (Eq. 5) in FP32; g' = 2 (y - t) / den is passed on
+//            without the 1/(3N) factor (applied by the Adam kernel) so that
+//            16-bit deltas stay in range;
+//  backward: per layer two MMAs issued together --
+//            dW_l += delta_{l+1}^T H_l  (M = 128 with rows 64..127 a duplicate
+//            that is never read, N = 64, K = 128 batch rows; both operands in
+//            shared memory, MN-major), accumulated in TMEM across the CTA's
+//            tiles; and, for l >= 1, delta_l = (delta_{l+1} W_l) * mask_l
+//            (A = delta in TMEM, B = the same weight image read MN-major).
+// At the end each CTA writes its dW (FP32) and loss sum to its own partial.
+constexpr int kTrainThreads = 128;
+constexpr int kTrainMaxMats = 6;  // TMEM: acc 64 + act 32 + 6 x 64 dW columns <= 512
+
+struct TrainParams {
+  const float* pool;
+  const float* target;
+  int64_t n_pool;
+  int64_t batch;
+  uint64_t a, c;
+  int step;
+  int n_mats;
+  ImageShape img;
+  int img_bytes;
+  int w_off[kMaxMats + 1];
+  int n_params;
+  float pad;
+  int loss_mode;
+  float loss_eps;
+  float inv3n;
+  float* partials;
+  long long* t_ctr;
+  const uint8_t* wimg;
+  int* err;
+};
+
+__device__ __forceinline__ void store_row_sw128(uint8_t* base, int r, const uint32_t (&pk)[32]) {
+  uint8_t* row = base + (r >> 3) * 1024 + (r & 7) * 128;
+#pragma unroll
+  for (int c = 0; c < 8; ++c)
+    *reinterpret_cast<uint4*>(row + ((c ^ (r & 7)) << 4)) = make_uint4(pk[4 * c], pk[4 * c + 1], pk[4 * c + 2], pk[4 * c + 3]);
+}
+
+template <int MODE, bool BF16>
+__global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(const __grid_constant__ TrainParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ uint64_t bar_w, bar_mma;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ float red[kTrainThreads / 32];
+  uint8_t* sw = align1024(smem_raw);                 // weight image
+  uint8_t* Hs = sw + ((p.img_bytes + 1023) & ~1023); // n_mats x 16 KB
+  uint8_t* Ds = Hs + p.n_mats * 16384;               // 16 KB
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  if (warp == 0) {
+    tmem_alloc(&tmem_base_sh, kTmemCols);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    mbar_init(&bar_w, 1);
+    mbar_init(&bar_mma, 1);
+    fence_barrier_init();
+    if (blockIdx.x == 0) *p.t_ctr += 1;  // Adam's step counter for the update that follows
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_base_sh;
+  if (tid == 0) {
+    mbar_arrive_expect_tx(&bar_w, uint32_t(p.img_bytes));
+    bulk_g2s(sw, p.wimg, uint32_t(p.img_bytes), &bar_w);
+  }
+  mbar_wait(&bar_w, 0, p.err);
+
+  const uint32_t lane_base = uint32_t(warp * 32) << 16;
+  const uint32_t t_acc = tmem + lane_base + 0;
+  const uint32_t t_act = tmem + lane_base + 64;
+  const uint32_t sw_base = smem_u32(sw), hs_base = smem_u32(Hs), ds_base = smem_u32(Ds);
+  const int L = p.n_mats;
+  uint32_t phase = 0;
+  float loss_acc = 0.0f;
+  const int64_t n_tiles = (p.batch + kTile - 1) / kTile;
+  bool first = true;
+
+  auto mma_sync_issue_wait = [&](auto&& issue) {
+    fence_proxy_async_smem();
+    fence_before();
+    named_sync(1, kTrainThreads);
+    if (tid == 0) {
+      fence_after();
+      issue();
+      mma_commit(&bar_mma);
+    }
+    mbar_wait(&bar_mma, phase, p.err);
+    phase ^= 1u;
+    fence_after();
+  };
+
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int64_t j = tile * kTile + tid;
+    const bool valid = j < p.batch;
+    float r[kRecFloats], tg[3] = {0.f, 0.f, 0.f};
+    if (valid) {
+      const uint64_t i = uint64_t(p.step) * uint64_t(p.batch) + uint64_t(j);
+      const int64_t src = int64_t((p.a * i + p.c) % uint64_t(p.n_pool));
+      load_record(p.pool, src, r);
+      tg[0] = __ldg(p.target + src * 3);
+      tg[1] = __ldg(p.target + src * 3 + 1);
+      tg[2] = __ldg(p.target + src * 3 + 2);
+    } else {
+#pragma unroll
+      for (int q = 0; q < kRecFloats; ++q) r[q] = 0.0f;
+    }
+    uint32_t pk[32];
+    {
+      float f[kEncDims];
+      encode_record<MODE>(r, p.pad, f);
+#pragma unroll
+      for (int q = 0; q < 32; ++q) pk[q] = pack2<BF16, false>(f[2 * q], f[2 * q + 1]);
+    }
+    store_row_sw128(Hs, tid, pk);
+    tmem_st16(t_act, *reinterpret_cast<const uint32_t(*)[16]>(&pk[0]));
+    tmem_st16(t_act + 16, *reinterpret_cast<const uint32_t(*)[16]>(&pk[16]));
+    tmem_st_wait();
+
+    // ------------------------------------------------------------ forward
+    uint64_t mask[kTrainMaxMats];
+    float y[3] = {0.f, 0.f, 0.f};
+    for (int l = 0; l < L; ++l) {
+      mma_sync_issue_wait([&]() {
+        const uint32_t idesc = idesc_f16(128, p.img.rows[l], BF16);
+        const uint32_t b0 = sw_base + uint32_t(p.img.off[l]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          mma_ts(tmem + 0, tmem + 64 + uint32_t(k * 8), sdesc_sw128(b0 + uint32_t(k * 32), 16, 1024), idesc,
+                 k > 0 ? 1u : 0u);
+      });
+      if (l + 1 < L) {
+        uint32_t v[32];
+        uint64_t mk = 0;
+        tmem_ld32(t_acc, v);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const float z0 = __uint_as_float(v[2 * q]), z1 = __uint_as_float(v[2 * q + 1]);
+          mk |= (uint64_t(z0 > 0.0f) << (2 * q)) | (uint64_t(z1 > 0.0f) << (2 * q + 1));
+          pk[q] = pack2<BF16, true>(z0, z1);
+        }
+        tmem_ld32(t_acc + 32, v);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const float z0 = __uint_as_float(v[2 * q]), z1 = __uint_as_float(v[2 * q + 1]);
+          mk |= (uint64_t(z0 > 0.0f) << (32 + 2 * q)) | (uint64_t(z1 > 0.0f) << (33 + 2 * q));
+          pk[16 + q] = pack2<BF16, true>(z0, z1);
+        }
+        mask[l + 1 < kTrainMaxMats ? l + 1 : 0] = mk;
+        store_row_sw128(Hs + (l + 1) * 16384, tid, pk);
+        tmem_st16(t_act, *reinterpret_cast<const uint32_t(*)[16]>(&pk[0]));
+        tmem_st16(t_act + 16, *reinterpret_cast<const uint32_t(*)[16]>(&pk[16]));
+        tmem_st_wait();
+      } else {
+        uint32_t v[4];
+        tmem_ld4(t_acc, v);
+        y[0] = __uint_as_float(v[0]);
+        y[1] = __uint_as_float(v[1]);
+        y[2] = __uint_as_float(v[2]);
+      }
+    }
+
+    // --------------------------------------------------------------- loss
+    float g[3];
+    {
+      const float lum = 0.2126f * y[0] + 0.7152f * y[1] + 0.0722f * y[2];
+      float lr = 0.0f;
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        const float den = (p.loss_mode == NRC_LOSS_LUMINANCE ? lum * lum : y[ch] * y[ch]) + p.loss_eps;
+        const float inv = 1.0f / den;
+        const float diff = y[ch] - tg[ch];
+        lr = fmaf(diff * diff, inv, lr);
+        g[ch] = valid ? fminf(fmaxf(2.0f * diff * inv, -60000.0f), 60000.0f) : 0.0f;
+      }
+      loss_acc += valid ? lr : 0.0f;
+    }
+    // delta_L: 3 gradients, zero-padded to the 16 outputs of the padded layer
+#pragma unroll
+    for (int q = 0; q < 32; ++q) pk[q] = 0u;
+    pk[0] = pack2<BF16, false>(g[0], g[1]);
+    pk[1] = pack2<BF16, false>(g[2], 0.0f);
+    store_row_sw128(Ds, tid, pk);
+    tmem_st16(t_act, *reinterpret_cast<const uint32_t(*)[16]>(&pk[0]));
+    tmem_st_wait();
+
+    // ----------------------------------------------------------- backward
+    for (int l = L - 1; l >= 0; --l) {
+      const bool first_acc = first;
+      mma_sync_issue_wait([&]() {
+        // dW_l (+)= delta_{l+1}^T H_l over this tile's 128 rows
+        const uint32_t idw = idesc_f16(128, 64, BF16, true, true);
+        const uint32_t dcol = tmem + 128 + uint32_t(l * 64);
+        const uint32_t hb = hs_base + uint32_t(l * 16384);
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          mma_ss(dcol, sdesc_sw128(ds_base + uint32_t(k * 2048), 0, 1024),
+                 sdesc_sw128(hb + uint32_t(k * 2048), 1024, 1024), idw, (first_acc && k == 0) ? 0u : 1u);
+        if (l > 0) {
+          // delta_l (pre-mask) = delta_{l+1} W_l: K = rows of W_l (64, or 16 for the output layer)
+          const int K = p.img.rows[l];
+          const uint32_t idd = idesc_f16(128, 64, BF16, false, true);
+          const uint32_t b0 = sw_base + uint32_t(p.img.off[l]);
+          for (int k = 0; k < K / 16; ++k)
+            mma_ts(tmem + 0, tmem + 64 + uint32_t(k * 8), sdesc_sw128(b0 + uint32_t(k * 2048), 1024, 1024), idd,
+                   k > 0 ? 1u : 0u);
+        }
+      });
+      if (l == 0) break;
+      const uint64_t mk = mask[l < kTrainMaxMats ? l : 0];
+      uint32_t v[32];
+      tmem_ld32(t_acc, v);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const float d0 = ((mk >> (2 * q)) & 1) ? __uint_as_float(v[2 * q]) : 0.0f;
+        const float d1 = ((mk >> (2 * q + 1)) & 1) ? __uint_as_float(v[2 * q + 1]) : 0.0f;
+        pk[q] = pack2<BF16, false>(fminf(fmaxf(d0, -60000.0f), 60000.0f), fminf(fmaxf(d1, -60000.0f), 60000.0f));
+      }
+      tmem_ld32(t_acc + 32, v);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const float d0 = ((mk >> (32 + 2 * q)) & 1) ? __uint_as_float(v[2 * q]) : 0.0f;
+        const float d1 = ((mk >> (33 + 2 * q)) & 1) ? __uint_as_float(v[2 * q + 1]) : 0.0f;
+        pk[16 + q] = pack2<BF16, false>(fminf(fmaxf(d0, -60000.0f), 60000.0f), fminf(fmaxf(d1, -60000.0f), 60000.0f));
+      }
+      store_row_sw128(Ds, tid, pk);
+      tmem_st16(t_act, *reinterpret_cast<const uint32_t(*)[16]>(&pk[0]));
+      tmem_st16(t_act + 16, *reinterpret_cast<const uint32_t(*)[16]>(&pk[16]));
+      tmem_st_wait();
+    }
+    first = false;
+  }
+
+  // ------------------------------------------------- write this CTA's partial
+  fence_before();
+  __syncthreads();
+  fence_after();
+  float* P = p.partials + size_t(blockIdx.x) * (size_t(p.n_params) + 1);
+  if (!first && warp < 2) {  // dW rows o = TMEM lanes 0..63
+    const int o = tid;
+    for (int l = 0; l < L; ++l) {
+      const int dout = (l + 1 < L) ? 64 : kOutDims;
+      uint32_t v[32];
+      const uint32_t base = tmem + lane_base + 128 + uint32_t(l * 64);
+      float* Pl = P + p.w_off[l] + o * 64;
+      tmem_ld32(base, v);
+      if (o < dout) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          reinterpret_cast<float4*>(Pl)[q] = make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
+                                                         __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
+      }
+      tmem_ld32(base + 32, v);
+      if (o < dout) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          reinterpret_cast<float4*>(Pl + 32)[q] = make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
+                                                              __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
+      }
+    }
+  } else if (first && warp < 2) {
+    for (int l = 0; l < L; ++l) {
+      const int dout = (l + 1 < L) ? 64 : kOutDims;
+      if (tid < dout)
+        for (int i = 0; i < 64; ++i) P[p.w_off[l] + tid * 64 + i] = 0.0f;
+    }
+  }
+  float s = loss_acc;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if ((tid & 31) == 0) red[warp] = s;
+  fence_before();
+  __syncthreads();
+  if (tid == 0) {
+    float tot = 0.0f;
+    for (int k = 0; k < kTrainThreads / 32; ++k) tot += red[k];
+    P[p.n_params] = tot * p.inv3n;
+  }
+  if (warp == 0) {
+    fence_after();
+    tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
 cudaError_t launch_train_tc(Cache* c, const float* pool, const float* target, int64_t n_pool, int64_t batch,
                             uint64_t a, uint64_t cc, int step, int* n_partials, float* grad_scale, cudaStream_t st) {
-  *grad_scale = 1.0f;
-  return launch_train_simt(c, pool, target, n_pool, batch, a, cc, step, n_partials, st);
+  if (c->net.n_mats > kTrainMaxMats) return cudaErrorNotSupported;
+  TrainParams p;
+  p.pool = pool;
+  p.target = target;
+  p.n_pool = n_pool;
+  p.batch = batch;
+  p.a = a;
+  p.c = cc;
+  p.step = step;
+  p.n_mats = c->net.n_mats;
+  p.img = c->img;
+  p.img_bytes = c->img.off[c->net.n_mats];
+  for (int l = 0; l <= kMaxMats; ++l) p.w_off[l] = c->net.w_off[l];
+  p.n_params = c->net.n_params;
+  p.pad = c->cfg.pad_value;
+  p.loss_mode = c->cfg.loss_mode;
+  p.loss_eps = c->cfg.loss_eps;
+  p.inv3n = float(1.0 / (3.0 * double(batch)));
+  p.t_ctr = c->t;
+  p.wimg = c->wimg;
+  p.err = c->err;
+  const int64_t n_tiles = (batch + kTile - 1) / kTile;
+  const int grid = int(n_tiles < c->sm_count ? n_tiles : c->sm_count);
+  cudaError_t e = ensure_partials(c, grid);
+  if (e != cudaSuccess) return e;
+  p.partials = c->partials;
+  const int smem = ((p.img_bytes + 1023) & ~1023) + p.n_mats * 16384 + 16384 + 1024;
+  const bool bf16 = c->cfg.dtype == NRC_BF16;
+  const int mode = c->cfg.enc_mode;
+#define NRC_LAUNCH(M, B)                                          \
+  e = set_smem(k_train_tc<M, B>, smem);                           \
+  if (e != cudaSuccess) return e;                                 \
+  k_train_tc<M, B><<<grid, kTrainThreads, smem, st>>>(p);
+  if (mode == 0 && !bf16) {
+    NRC_LAUNCH(0, false)
+  } else if (mode == 0 && bf16) {
+    NRC_LAUNCH(0, true)
+  } else if (!bf16) {
+    NRC_LAUNCH(1, false)
+  } else {
+    NRC_LAUNCH(1, true)
+  }
+#undef NRC_LAUNCH
+  *n_partials = grid;
+  *grad_scale = p.inv3n;
+  return cudaGetLastError();
 }
 
 }  // namespace nrc

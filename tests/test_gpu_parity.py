@@ -2,13 +2,14 @@
 
 Tolerances: record indexing and gather bit-exact; encoding <= 1e-6 absolute;
 outputs, loss and gradients <= 1e-5 relative (FP32 path) and <= 2e-2 (FP16 /
-BF16 tensor-core path), per output with the tau = 1e-3 * rms floor.
+BF16 tensor-core path), per output, with the relative error floored at the
+batch rms (see parity.py for why the floor is needed).
 """
 import numpy as np
 import pytest
 
 from paper_2106_12372_gb300 import synth
-from parity import rel_err
+from parity import rel_err, stats
 
 pytestmark = pytest.mark.gpu
 
@@ -82,8 +83,9 @@ def test_infer_small(dtype, n):
     cache = nrc.Cache(dtype=dtype)
     cache.set_state(w0)
     got = cache.infer(dev(rec)).cpu().numpy()
-    err = rel_err(got, ref)
-    assert err.max() <= TOL[dtype], (dtype, n, err.max())
+    st = stats(got, ref)
+    print("infer", dtype, n, st)
+    assert st["max"] <= TOL[dtype], (dtype, n, st)
     cache.check_error()
 
 
@@ -122,8 +124,9 @@ def test_infer_full_frame_sampled():
     got = cache.infer(dev(rec)).cpu().numpy()
     idx = np.concatenate([np.random.default_rng(0).choice(n, 4000, replace=False), [0, n - 1, n - 128, 127, 128]])
     ref = O.infer(w0, DIMS, rec[idx])
-    err = rel_err(got[idx], ref)
-    assert err.max() <= TOL["fp16"]
+    st = stats(got[idx], ref)
+    print("full frame fp16", st)
+    assert st["max"] <= TOL["fp16"], st
     assert np.all(np.isfinite(got))
 
 
@@ -158,7 +161,7 @@ def test_train_step_fp32(n_pool, batch, step, loss_mode):
     assert t == 1
     assert abs(loss - ref_loss) <= 1e-5 * abs(ref_loss)
     g = m.astype(np.float64) / (1.0 - 0.9)  # after step 1, m = (1 - beta1) g
-    assert rel_err(g, ref_g).max() <= 1e-5 * 10  # m carries one extra FP32 rounding of (1-b1)*g
+    assert rel_err(g, ref_g).max() <= 1e-5, stats(g, ref_g)
     # one-step weights: elements with |g| > 1e-3 rms(g) must match; the others may flip sign (Adam, t = 1)
     keep = np.abs(ref_g) > 1e-3 * np.sqrt(np.mean(ref_g ** 2))
     assert np.max(np.abs(w[keep] - st.W[keep]) / np.abs(st.W[keep]).clip(1e-3)) <= 1e-5
@@ -169,8 +172,19 @@ def test_train_step_16bit(dtype):
     ref_loss, ref_g, st, loss, w, m, v, t = _one_step(dtype, 65536, 16384, 3, 70)
     assert abs(loss - ref_loss) <= 2e-2 * abs(ref_loss)
     g = m.astype(np.float64) / (1.0 - 0.9)
-    err = np.abs(g - ref_g) / np.sqrt(np.mean(ref_g ** 2))
-    assert np.median(err) <= 2e-2 and np.mean(err) <= 2e-2
+    print("train", dtype, "loss", loss, ref_loss, "grad", stats(g, ref_g))
+    assert rel_err(g, ref_g).max() <= 2e-2, stats(g, ref_g)
+
+
+@pytest.mark.parametrize("n_pool,batch,step", [(4096, 1000, 1), (65536, 65536, 0), (2048, 128, 5)])
+def test_train_step_16bit_shapes(n_pool, batch, step):
+    # ragged last tile, several tiles per CTA (dW accumulated in TMEM across tiles), a single tile
+    ref_loss, ref_g, st, loss, w, m, v, t = _one_step("fp16", n_pool, batch, step, 75 + batch)
+    g = m.astype(np.float64) / (1.0 - 0.9)
+    print("train fp16", n_pool, batch, "loss", loss, ref_loss, "grad", stats(g, ref_g))
+    assert t == 1
+    assert abs(loss - ref_loss) <= 2e-2 * abs(ref_loss)
+    assert rel_err(g, ref_g).max() <= 2e-2, stats(g, ref_g)
 
 
 def test_train_steps_match_oracle_curve_fp32():
@@ -249,7 +263,7 @@ def test_plain_path_matches_oracle():
     cache.train_step(dev(pool), dev(tgt), 2048, fs, 1, loss_out=loss)
     w, m, v, t = cache.get_state()
     assert t == 1 and abs(loss.item() - ref_loss) <= 1e-5 * ref_loss
-    assert rel_err(m / 0.1, ref_g).max() <= 1e-4
+    assert rel_err(m / 0.1, ref_g).max() <= 1e-5
 
 
 # ---------------------------------------------------------------- boundary
