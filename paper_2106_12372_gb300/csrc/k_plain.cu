@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(kPR) k_plain_loss(const float* __restrict__ Yh
   if (threadIdx.x == 0) {
     float tot = 0.0f;
     for (int k = 0; k < kPR / 32; ++k) tot += red[k];
-    partials[size_t(blockIdx.x) * (size_t(n_params) + 1) + n_params] = tot * inv3n;
+    partials[size_t(blockIdx.x) * partial_stride(n_params) + n_params] = tot * inv3n;
   }
 }
 
@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(256) k_plain_dw(const float* __restrict__ D, c
 #pragma unroll
       for (int i = 0; i < 4; ++i) acc[j][i] = fmaf(a[j], b[i], acc[j][i]);
   }
-  float* P = partials + size_t(blockIdx.x) * (size_t(n_params) + 1) + w_off;
+  float* P = partials + size_t(blockIdx.x) * partial_stride(n_params) + w_off;
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const int o = to * 4 + j;

@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(kTrainRows) k_train_simt(const float* __restri
     g[0] = g[1] = g[2] = 0.0f;
     loss_row = 0.0f;
   }
-  float* P = partials + size_t(blockIdx.x) * size_t(net.n_params + 1);
+  float* P = partials + size_t(blockIdx.x) * partial_stride(net.n_params);
   // backward: d holds delta_{l+1} of this row
   float d[64];
 #pragma unroll
@@ -404,7 +404,7 @@ __global__ void k_adam(float* __restrict__ w, float* __restrict__ m, float* __re
                        uint8_t* __restrict__ wimg, float grad_scale, float lr, float b1,
                        float b2, float eps, float* __restrict__ loss_out) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  const size_t stride = size_t(net.n_params) + 1;
+  const size_t stride = partial_stride(net.n_params);
   if (blockIdx.x == 0 && threadIdx.x == 0 && loss_out) {
     float s = 0.0f;
     for (int k = 0; k < n_partials; ++k) s += partials[size_t(k) * stride + net.n_params];

@@ -8,14 +8,16 @@
 //        the MMA's A operand.
 // The whole 16-bit weight image (Sec. 5 architecture; ~42 KB at width 64) is
 // bulk-copied into shared memory once per CTA and serves as the B operand of
-// every layer (K-major, 128-byte swizzle).  Per tile: the records are read
-// from HBM by the thread that owns the row, encoded in registers (Table 1,
-// Sec. 3.6) and stored to TMEM; then for each layer one thread issues
-// 4 x (M128 x N64 x K16) tcgen05.mma reading A from TMEM and B from shared
-// memory, commits to the warpgroup's mbarrier, and the warpgroup applies the
-// ReLU, rounds to 16 bit and writes the next layer's A back into TMEM.  The
-// output layer (N = 16, 3 used) is read back and stored as RGB.  Activations
-// never leave the SM.
+// every layer (K-major, 128-byte swizzle).  Per tile: each thread's 64-byte
+// record was prefetched into shared memory with cp.async while the previous
+// tile ran (double-buffered, 16-byte chunks rotated so that the row reads are
+// free of bank conflicts); it is encoded in registers (Table 1, Sec. 3.6) and
+// stored to TMEM; then for each layer one thread issues 4 x (M128 x N64 x
+// K16) tcgen05.mma reading A from TMEM and B from shared memory, commits to
+// the warpgroup's mbarrier, and the warpgroup applies the ReLU, rounds to 16
+// bit and writes the next layer's A back into TMEM.  The output layer
+// (N = 16, 3 used) is read back and stored as RGB.  Activations never leave
+// the SM.
 #include "tc_ptx.cuh"
 
 namespace nrc {
@@ -50,6 +52,7 @@ __global__ void __launch_bounds__(kInferThreads, 1) k_infer_tc(const __grid_cons
   __shared__ uint64_t bar_mma[kSlots];
   __shared__ uint32_t tmem_base_sh;
   uint8_t* sw = align1024(smem_raw);
+  uint8_t* recs = sw + ((p.img_bytes + 1023) & ~1023);  // [kSlots][2][128 rows][64 B]
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
   const int slot = tid >> 7;
@@ -72,7 +75,6 @@ __global__ void __launch_bounds__(kInferThreads, 1) k_infer_tc(const __grid_cons
     mbar_arrive_expect_tx(&bar_w, uint32_t(p.img_bytes));
     bulk_g2s(sw, p.wimg, uint32_t(p.img_bytes), &bar_w);
   }
-  mbar_wait(&bar_w, 0, p.err);
 
   const uint32_t lane_base = uint32_t((warp & 3) * 32) << 16;
   const uint32_t acc_col = uint32_t(slot * kSlotCols);
@@ -80,18 +82,43 @@ __global__ void __launch_bounds__(kInferThreads, 1) k_infer_tc(const __grid_cons
   const uint32_t t_acc = tmem + lane_base + acc_col;
   const uint32_t t_act = tmem + lane_base + act_col;
   const uint32_t sw_base = smem_u32(sw);
-  uint32_t phase = 0;
   const int64_t n_tiles = (p.n + kTile - 1) / kTile;
-
-  for (int64_t tile = int64_t(blockIdx.x) * kSlots + slot; tile < n_tiles; tile += int64_t(gridDim.x) * kSlots) {
-    const int64_t row = tile * kTile + rit;
-    float r[kRecFloats];
-    if (row < p.n) {
-      load_record(p.rec, row, r);
-    } else {
+  const int64_t stride = int64_t(gridDim.x) * kSlots;
+  // this thread's record row in each of the slot's two staging buffers
+  const uint32_t rec_row0 = smem_u32(recs) + uint32_t(slot * 2 * 8192 + rit * 64);
+  const uint32_t rot = uint32_t((rit >> 1) & 3);
+  auto prefetch = [&](int64_t t, int b) {
+    const int64_t row = t * kTile + rit;
+    const bool ok = t < n_tiles && row < p.n;
+    const float* src = p.rec + (ok ? row : 0) * kRecFloats;
 #pragma unroll
-      for (int q = 0; q < kRecFloats; ++q) r[q] = 0.0f;
+    for (int q = 0; q < 4; ++q)
+      cp_async16(rec_row0 + uint32_t(b * 8192) + ((uint32_t(q) ^ rot) << 4), src + 4 * q, ok ? 16u : 0u);
+    cp_async_commit();
+  };
+  int64_t tile = int64_t(blockIdx.x) * kSlots + slot;
+  int buf = 0;
+  prefetch(tile, buf);
+  mbar_wait(&bar_w, 0, p.err);
+  uint32_t phase = 0;
+
+  for (; tile < n_tiles; tile += stride) {
+    const int64_t row = tile * kTile + rit;
+    prefetch(tile + stride, buf ^ 1);
+    cp_async_wait<1>();  // this tile's record has landed (only this thread reads it)
+    float r[kRecFloats];
+    {
+      const uint8_t* rowp = recs + slot * 2 * 8192 + buf * 8192 + rit * 64;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 v = *reinterpret_cast<const float4*>(rowp + ((uint32_t(q) ^ rot) << 4));
+        r[4 * q] = v.x;
+        r[4 * q + 1] = v.y;
+        r[4 * q + 2] = v.z;
+        r[4 * q + 3] = v.w;
+      }
     }
+    buf ^= 1;
     uint32_t pk[16];
     {
       float f[kEncDims];
@@ -143,6 +170,7 @@ __global__ void __launch_bounds__(kInferThreads, 1) k_infer_tc(const __grid_cons
       }
     }
   }
+  cp_async_wait<0>();
   fence_before();
   __syncthreads();
   if (warp == 0) {
@@ -167,7 +195,7 @@ cudaError_t launch_infer_tc(Cache* c, const float* rec, int64_t n, float* rgb, c
   p.img = c->img;
   p.pad = c->cfg.pad_value;
   p.err = c->err;
-  const int smem = p.img_bytes + 1024;
+  const int smem = ((p.img_bytes + 1023) & ~1023) + kSlots * 2 * 8192 + 1024;
   const int64_t n_tiles = (n + kTile - 1) / kTile;
   const int64_t want = (n_tiles + kSlots - 1) / kSlots;
   const unsigned grid = unsigned(want < c->sm_count ? want : c->sm_count);
@@ -441,7 +469,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(const __grid_cons
   fence_before();
   __syncthreads();
   fence_after();
-  float* P = p.partials + size_t(blockIdx.x) * (size_t(p.n_params) + 1);
+  float* P = p.partials + size_t(blockIdx.x) * partial_stride(p.n_params);
   if (!first && warp < 2) {  // dW rows o = TMEM lanes 0..63
     const int o = tid;
     for (int l = 0; l < L; ++l) {

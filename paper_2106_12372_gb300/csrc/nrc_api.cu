@@ -102,7 +102,7 @@ cudaError_t ensure_partials(Cache* c, int count) {
   cudaFree(c->partials);
   c->partials = nullptr;
   c->max_partials = 0;
-  e = cudaMalloc(&c->partials, size_t(count) * (size_t(c->net.n_params) + 1) * 4);
+  e = cudaMalloc(&c->partials, size_t(count) * partial_stride(c->net.n_params) * 4);
   if (e == cudaSuccess) c->max_partials = count;
   return e;
 }

@@ -30,6 +30,13 @@ struct NetShape {
   int n_params;
 };
 
+// Elements between consecutive weight-gradient partials: the n_params
+// gradients, the loss sum, padded to a multiple of 4 floats so that every
+// partial starts 16-byte aligned (the tensor-core kernel stores float4).
+__host__ __device__ __forceinline__ size_t partial_stride(int n_params) {
+  return (size_t(n_params) + 1 + 3) & ~size_t(3);
+}
+
 // Byte layout of the 16-bit weight image for the tensor-core kernels: matrix
 // l is stored as N_l = round_up(d_{l+1}, 16) rows of K_l = d_l elements,
 // K-major with the 128-byte swizzle (8-row atoms of 1024 bytes; 16-byte chunk
@@ -50,7 +57,7 @@ struct Cache {
   float* v = nullptr;     // Adam second moment
   long long* t = nullptr; // Adam step counter (device)
   uint8_t* wimg = nullptr;        // 16-bit weight image (tensor-core path)
-  float* partials = nullptr;      // [max_partials][n_params + 1] weight-gradient + loss partials
+  float* partials = nullptr;      // [max_partials][partial_stride] weight-gradient partials; loss at [n_params]
   int max_partials = 0;
   int* err = nullptr;     // device error word
   // plain-path scratch (grown on demand)
