@@ -397,26 +397,58 @@ cudaError_t launch_train_simt(Cache* c, const float* pool, const float* target, 
 // scales them, and applies Adam (Sec. 5; Kingma & Ba 2015) with bias
 // correction to the FP32 master weights; writes the 16-bit copy into the
 // swizzled weight image when the cache computes in FP16/BF16.
+// A block handles 32 consecutive weights (one per lane, coalesced reads);
+// its 8 warps each sum every 8th partial, then warp 0 adds the 8 sums in
+// warp order.  Block 0's warp 1 also sums the loss slots.
+constexpr int kAdamGroups = 8;
+
 template <int IMG>  // 0: no image, 1: FP16, 2: BF16
-__global__ void k_adam(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
-                       const long long* __restrict__ t_ctr, const float* __restrict__ partials, int n_partials,
-                       const __grid_constant__ NetShape net, const __grid_constant__ ImageShape img,
-                       uint8_t* __restrict__ wimg, float grad_scale, float lr, float b1,
-                       float b2, float eps, float* __restrict__ loss_out) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  const size_t stride = partial_stride(net.n_params);
-  if (blockIdx.x == 0 && threadIdx.x == 0 && loss_out) {
-    float s = 0.0f;
-    for (int k = 0; k < n_partials; ++k) s += partials[size_t(k) * stride + net.n_params];
-    *loss_out = s;
+__global__ void __launch_bounds__(32 * kAdamGroups) k_adam(float* __restrict__ w, float* __restrict__ m,
+                                                           float* __restrict__ v, const long long* __restrict__ t_ctr,
+                                                           const float* __restrict__ partials, int n_partials,
+                                                           const __grid_constant__ NetShape net,
+                                                           const __grid_constant__ ImageShape img,
+                                                           uint8_t* __restrict__ wimg, float grad_scale, float lr,
+                                                           float b1, float b2, float eps, float* __restrict__ loss_out) {
+  __shared__ float red[kAdamGroups][32];
+  __shared__ float corr[2];
+  const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {  // bias corrections 1 - beta^t, once per block (FP64 is slow on this part)
+    const double t = double(*t_ctr);
+    corr[0] = float(1.0 - pow(double(b1), t));
+    corr[1] = float(1.0 - pow(double(b2), t));
   }
-  if (p >= net.n_params) return;
+  const size_t stride = partial_stride(net.n_params);
+  const int p = blockIdx.x * 32 + lane;
+  if (blockIdx.x == 0 && grp == 1 && loss_out) {
+    float s = 0.0f;
+    for (int k = lane; k < n_partials; k += 32) s += partials[size_t(k) * stride + net.n_params];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (lane == 0) *loss_out = s;
+  }
+  float part = 0.0f;
+  if (p < net.n_params) {
+    const float* src = partials + p;
+    int k = grp;
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+    for (; k + 3 * kAdamGroups < n_partials; k += 4 * kAdamGroups) {
+      a0 += src[size_t(k) * stride];
+      a1 += src[size_t(k + kAdamGroups) * stride];
+      a2 += src[size_t(k + 2 * kAdamGroups) * stride];
+      a3 += src[size_t(k + 3 * kAdamGroups) * stride];
+    }
+    for (; k < n_partials; k += kAdamGroups) a0 += src[size_t(k) * stride];
+    part = (a0 + a1) + (a2 + a3);
+  }
+  red[grp][lane] = part;
+  __syncthreads();
+  if (grp != 0 || p >= net.n_params) return;
   float g = 0.0f;
-  for (int k = 0; k < n_partials; ++k) g += partials[size_t(k) * stride + p];
+#pragma unroll
+  for (int q = 0; q < kAdamGroups; ++q) g += red[q][lane];
   g *= grad_scale;
-  const double t = double(*t_ctr);
-  const float c1 = float(1.0 - pow(double(b1), t));
-  const float c2 = float(1.0 - pow(double(b2), t));
+  const float c1 = corr[0], c2 = corr[1];
   const float mn = fmaf(b1, m[p], (1.0f - b1) * g);
   const float vn = fmaf(b2, v[p], (1.0f - b2) * g * g);
   m[p] = mn;
@@ -437,8 +469,8 @@ __global__ void k_adam(float* __restrict__ w, float* __restrict__ m, float* __re
 }
 
 cudaError_t launch_adam(Cache* c, int n_partials, float grad_scale, float* loss_out, cudaStream_t st) {
-  const int threads = 256;
-  const int blocks = (c->net.n_params + threads - 1) / threads;
+  const int threads = 32 * kAdamGroups;
+  const int blocks = (c->net.n_params + 31) / 32;
   const nrc_config& k = c->cfg;
   if (k.dtype == NRC_FP16)
     k_adam<1><<<blocks, threads, 0, st>>>(c->w, c->m, c->v, c->t, c->partials, n_partials, c->net, c->img, c->wimg,

@@ -222,11 +222,13 @@ cudaError_t launch_infer_tc(Cache* c, const float* rec, int64_t n, float* rgb, c
 // ------------------------------------------------------------- training
 // Fused training step on the tensor cores (Sec. 4, training the fully fused
 // network; Eq. 5; the weight-gradient contraction the paper leaves to a
-// split-k GEMM).  One warpgroup per CTA, one 128-row batch tile at a time;
-// each thread owns one gathered record (Sec. 3.5 shuffle).
+// split-k GEMM).  Two warpgroups per CTA work on one 128-row batch tile at a
+// time: thread (h, r) owns gathered record r (Sec. 3.5 shuffle) and column
+// half h (features / neurons 32h .. 32h+31) of every epilogue.
 //  forward : H_{l+1} = ReLU(W_l H_l) as in inference; every H_l is also kept
-//            in shared memory (16-bit, 128-byte swizzled rows) for the
-//            weight gradients, and the sign masks [Z_l > 0] stay in registers;
+//            in shared memory (16-bit, 128-byte swizzled rows): it is the B
+//            operand of the weight gradient and, being post-ReLU, its nonzero
+//            entries are the ReLU mask [Z_l > 0] of the backward pass;
 //  loss    : relative L2 (Eq. 5) in FP32; g' = 2 (y - t) / den is passed on
 //            without the 1/(3N) factor (applied by the Adam kernel) so that
 //            16-bit deltas stay in range;
@@ -237,7 +239,7 @@ cudaError_t launch_infer_tc(Cache* c, const float* rec, int64_t n, float* rgb, c
 //            tiles; and, for l >= 1, delta_l = (delta_{l+1} W_l) * mask_l
 //            (A = delta in TMEM, B = the same weight image read MN-major).
 // At the end each CTA writes its dW (FP32) and loss sum to its own partial.
-constexpr int kTrainThreads = 128;
+constexpr int kTrainThreads = 256;
 constexpr int kTrainMaxMats = 6;  // TMEM: acc 64 + act 32 + 6 x 64 dW columns <= 512
 
 struct TrainParams {
@@ -262,11 +264,44 @@ struct TrainParams {
   int* err;
 };
 
-__device__ __forceinline__ void store_row_sw128(uint8_t* base, int r, const uint32_t (&pk)[32]) {
+// Writes 16-byte chunks c0 .. c0+3 of row r of a 128-byte-swizzled tile.
+__device__ __forceinline__ void store_half_row_sw128(uint8_t* base, int r, int c0, const uint32_t (&pk)[16]) {
   uint8_t* row = base + (r >> 3) * 1024 + (r & 7) * 128;
 #pragma unroll
-  for (int c = 0; c < 8; ++c)
-    *reinterpret_cast<uint4*>(row + ((c ^ (r & 7)) << 4)) = make_uint4(pk[4 * c], pk[4 * c + 1], pk[4 * c + 2], pk[4 * c + 3]);
+  for (int c = 0; c < 4; ++c)
+    *reinterpret_cast<uint4*>(row + (((c0 + c) ^ (r & 7)) << 4)) =
+        make_uint4(pk[4 * c], pk[4 * c + 1], pk[4 * c + 2], pk[4 * c + 3]);
+}
+
+__device__ __forceinline__ void load_half_row_sw128(const uint8_t* base, int r, int c0, uint32_t (&pk)[16]) {
+  const uint8_t* row = base + (r >> 3) * 1024 + (r & 7) * 128;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const uint4 v = *reinterpret_cast<const uint4*>(row + (((c0 + c) ^ (r & 7)) << 4));
+    pk[4 * c] = v.x;
+    pk[4 * c + 1] = v.y;
+    pk[4 * c + 2] = v.z;
+    pk[4 * c + 3] = v.w;
+  }
+}
+
+// delta pair from two FP32 pre-activations: rounded to 16 bit, clamped to the
+// finite FP16 range, zeroed where the stored post-ReLU activation is zero.
+template <bool BF16>
+__device__ __forceinline__ uint32_t masked_delta2(float d0, float d1, uint32_t h2) {
+  const uint32_t raw = pack2<BF16, false>(d0, d1);
+  if (BF16) {
+    const __nv_bfloat162 d = *reinterpret_cast<const __nv_bfloat162*>(&raw);
+    const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&h2);
+    const __nv_bfloat162 r = __hmul2(d, __hgt2(h, __float2bfloat162_rn(0.0f)));
+    return *reinterpret_cast<const uint32_t*>(&r);
+  } else {
+    const __half2 lim = __float2half2_rn(60000.0f);
+    const __half2 d = __hmax2(__hmin2(*reinterpret_cast<const __half2*>(&raw), lim), __hneg2(lim));
+    const __half2 h = *reinterpret_cast<const __half2*>(&h2);
+    const __half2 r = __hmul2(d, __hgt2(h, __float2half2_rn(0.0f)));
+    return *reinterpret_cast<const uint32_t*>(&r);
+  }
 }
 
 template <int MODE, bool BF16>
@@ -274,12 +309,14 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(const __grid_cons
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t bar_w, bar_mma;
   __shared__ uint32_t tmem_base_sh;
-  __shared__ float red[kTrainThreads / 32];
+  __shared__ float red[4];
   uint8_t* sw = align1024(smem_raw);                 // weight image
   uint8_t* Hs = sw + ((p.img_bytes + 1023) & ~1023); // n_mats x 16 KB
   uint8_t* Ds = Hs + p.n_mats * 16384;               // 16 KB
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
+  const int half = tid >> 7;  // column half of this thread
+  const int r = tid & 127;    // row in tile == TMEM lane
   if (warp == 0) {
     tmem_alloc(&tmem_base_sh, kTmemCols);
     tmem_relinquish();
@@ -298,11 +335,11 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(const __grid_cons
     mbar_arrive_expect_tx(&bar_w, uint32_t(p.img_bytes));
     bulk_g2s(sw, p.wimg, uint32_t(p.img_bytes), &bar_w);
   }
-  mbar_wait(&bar_w, 0, p.err);
+  bool have_w = false;  // the weight copy is waited for before the first MMA
 
-  const uint32_t lane_base = uint32_t(warp * 32) << 16;
-  const uint32_t t_acc = tmem + lane_base + 0;
-  const uint32_t t_act = tmem + lane_base + 64;
+  const uint32_t lane_base = uint32_t((warp & 3) * 32) << 16;
+  const uint32_t t_acc = tmem + lane_base + uint32_t(32 * half);        // my 32 accumulator columns
+  const uint32_t t_act = tmem + lane_base + 64 + uint32_t(16 * half);   // my 16 packed activation columns
   const uint32_t sw_base = smem_u32(sw), hs_base = smem_u32(Hs), ds_base = smem_u32(Ds);
   const int L = p.n_mats;
   uint32_t phase = 0;
@@ -325,34 +362,38 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(const __grid_cons
   };
 
   for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    const int64_t j = tile * kTile + tid;
+    const int64_t j = tile * kTile + r;
     const bool valid = j < p.batch;
-    float r[kRecFloats], tg[3] = {0.f, 0.f, 0.f};
+    float rec[kRecFloats], tg[3] = {0.f, 0.f, 0.f};
     if (valid) {
       const uint64_t i = uint64_t(p.step) * uint64_t(p.batch) + uint64_t(j);
       const int64_t src = int64_t((p.a * i + p.c) % uint64_t(p.n_pool));
-      load_record(p.pool, src, r);
-      tg[0] = __ldg(p.target + src * 3);
-      tg[1] = __ldg(p.target + src * 3 + 1);
-      tg[2] = __ldg(p.target + src * 3 + 2);
+      load_record(p.pool, src, rec);
+      if (half == 0) {
+        tg[0] = __ldg(p.target + src * 3);
+        tg[1] = __ldg(p.target + src * 3 + 1);
+        tg[2] = __ldg(p.target + src * 3 + 2);
+      }
     } else {
 #pragma unroll
-      for (int q = 0; q < kRecFloats; ++q) r[q] = 0.0f;
+      for (int q = 0; q < kRecFloats; ++q) rec[q] = 0.0f;
     }
-    uint32_t pk[32];
+    uint32_t pk[16];
     {
-      float f[kEncDims];
-      encode_record<MODE>(r, p.pad, f);
+      float f[32];
+      encode_record_half<MODE>(rec, p.pad, half, f);
 #pragma unroll
-      for (int q = 0; q < 32; ++q) pk[q] = pack2<BF16, false>(f[2 * q], f[2 * q + 1]);
+      for (int q = 0; q < 16; ++q) pk[q] = pack2<BF16, false>(f[2 * q], f[2 * q + 1]);
     }
-    store_row_sw128(Hs, tid, pk);
-    tmem_st16(t_act, *reinterpret_cast<const uint32_t(*)[16]>(&pk[0]));
-    tmem_st16(t_act + 16, *reinterpret_cast<const uint32_t(*)[16]>(&pk[16]));
+    store_half_row_sw128(Hs, r, 4 * half, pk);
+    tmem_st16(t_act, pk);
     tmem_st_wait();
+    if (!have_w) {
+      mbar_wait(&bar_w, 0, p.err);
+      have_w = true;
+    }
 
     // ------------------------------------------------------------ forward
-    uint64_t mask[kTrainMaxMats];
     float y[3] = {0.f, 0.f, 0.f};
     for (int l = 0; l < L; ++l) {
       mma_sync_issue_wait([&]() {
@@ -365,27 +406,13 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(const __grid_cons
       });
       if (l + 1 < L) {
         uint32_t v[32];
-        uint64_t mk = 0;
         tmem_ld32(t_acc, v);
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const float z0 = __uint_as_float(v[2 * q]), z1 = __uint_as_float(v[2 * q + 1]);
-          mk |= (uint64_t(z0 > 0.0f) << (2 * q)) | (uint64_t(z1 > 0.0f) << (2 * q + 1));
-          pk[q] = pack2<BF16, true>(z0, z1);
-        }
-        tmem_ld32(t_acc + 32, v);
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const float z0 = __uint_as_float(v[2 * q]), z1 = __uint_as_float(v[2 * q + 1]);
-          mk |= (uint64_t(z0 > 0.0f) << (32 + 2 * q)) | (uint64_t(z1 > 0.0f) << (33 + 2 * q));
-          pk[16 + q] = pack2<BF16, true>(z0, z1);
-        }
-        mask[l + 1 < kTrainMaxMats ? l + 1 : 0] = mk;
-        store_row_sw128(Hs + (l + 1) * 16384, tid, pk);
-        tmem_st16(t_act, *reinterpret_cast<const uint32_t(*)[16]>(&pk[0]));
-        tmem_st16(t_act + 16, *reinterpret_cast<const uint32_t(*)[16]>(&pk[16]));
+        for (int q = 0; q < 16; ++q) pk[q] = pack2<BF16, true>(__uint_as_float(v[2 * q]), __uint_as_float(v[2 * q + 1]));
+        store_half_row_sw128(Hs + (l + 1) * 16384, r, 4 * half, pk);
+        tmem_st16(t_act, pk);
         tmem_st_wait();
-      } else {
+      } else if (half == 0) {
         uint32_t v[4];
         tmem_ld4(t_acc, v);
         y[0] = __uint_as_float(v[0]);
@@ -395,10 +422,12 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(const __grid_cons
     }
 
     // --------------------------------------------------------------- loss
-    float g[3];
-    {
+    // delta_L: 3 gradients, zero-padded to the 16 outputs of the padded layer
+#pragma unroll
+    for (int q = 0; q < 16; ++q) pk[q] = 0u;
+    if (half == 0) {
       const float lum = 0.2126f * y[0] + 0.7152f * y[1] + 0.0722f * y[2];
-      float lr = 0.0f;
+      float lr = 0.0f, g[3];
 #pragma unroll
       for (int ch = 0; ch < 3; ++ch) {
         const float den = (p.loss_mode == NRC_LOSS_LUMINANCE ? lum * lum : y[ch] * y[ch]) + p.loss_eps;
@@ -408,14 +437,11 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(const __grid_cons
         g[ch] = valid ? fminf(fmaxf(2.0f * diff * inv, -60000.0f), 60000.0f) : 0.0f;
       }
       loss_acc += valid ? lr : 0.0f;
+      pk[0] = pack2<BF16, false>(g[0], g[1]);
+      pk[1] = pack2<BF16, false>(g[2], 0.0f);
     }
-    // delta_L: 3 gradients, zero-padded to the 16 outputs of the padded layer
-#pragma unroll
-    for (int q = 0; q < 32; ++q) pk[q] = 0u;
-    pk[0] = pack2<BF16, false>(g[0], g[1]);
-    pk[1] = pack2<BF16, false>(g[2], 0.0f);
-    store_row_sw128(Ds, tid, pk);
-    tmem_st16(t_act, *reinterpret_cast<const uint32_t(*)[16]>(&pk[0]));
+    store_half_row_sw128(Ds, r, 4 * half, pk);
+    tmem_st16(t_act, pk);
     tmem_st_wait();
 
     // ----------------------------------------------------------- backward
@@ -441,75 +467,52 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(const __grid_cons
         }
       });
       if (l == 0) break;
-      const uint64_t mk = mask[l < kTrainMaxMats ? l : 0];
-      uint32_t v[32];
+      uint32_t v[32], h2[16];
       tmem_ld32(t_acc, v);
+      load_half_row_sw128(Hs + l * 16384, r, 4 * half, h2);
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const float d0 = ((mk >> (2 * q)) & 1) ? __uint_as_float(v[2 * q]) : 0.0f;
-        const float d1 = ((mk >> (2 * q + 1)) & 1) ? __uint_as_float(v[2 * q + 1]) : 0.0f;
-        pk[q] = pack2<BF16, false>(fminf(fmaxf(d0, -60000.0f), 60000.0f), fminf(fmaxf(d1, -60000.0f), 60000.0f));
-      }
-      tmem_ld32(t_acc + 32, v);
-#pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const float d0 = ((mk >> (32 + 2 * q)) & 1) ? __uint_as_float(v[2 * q]) : 0.0f;
-        const float d1 = ((mk >> (33 + 2 * q)) & 1) ? __uint_as_float(v[2 * q + 1]) : 0.0f;
-        pk[16 + q] = pack2<BF16, false>(fminf(fmaxf(d0, -60000.0f), 60000.0f), fminf(fmaxf(d1, -60000.0f), 60000.0f));
-      }
-      store_row_sw128(Ds, tid, pk);
-      tmem_st16(t_act, *reinterpret_cast<const uint32_t(*)[16]>(&pk[0]));
-      tmem_st16(t_act + 16, *reinterpret_cast<const uint32_t(*)[16]>(&pk[16]));
+      for (int q = 0; q < 16; ++q)
+        pk[q] = masked_delta2<BF16>(__uint_as_float(v[2 * q]), __uint_as_float(v[2 * q + 1]), h2[q]);
+      store_half_row_sw128(Ds, r, 4 * half, pk);
+      tmem_st16(t_act, pk);
       tmem_st_wait();
     }
     first = false;
   }
+
+  if (!have_w) mbar_wait(&bar_w, 0, p.err);  // never leave with the weight copy in flight
 
   // ------------------------------------------------- write this CTA's partial
   fence_before();
   __syncthreads();
   fence_after();
   float* P = p.partials + size_t(blockIdx.x) * partial_stride(p.n_params);
-  if (!first && warp < 2) {  // dW rows o = TMEM lanes 0..63
-    const int o = tid;
+  if ((warp & 3) < 2) {  // dW rows o = TMEM lanes 0..63; this thread writes columns 32h .. 32h+31
+    const int o = r;
     for (int l = 0; l < L; ++l) {
       const int dout = (l + 1 < L) ? 64 : kOutDims;
-      uint32_t v[32];
-      const uint32_t base = tmem + lane_base + 128 + uint32_t(l * 64);
-      float* Pl = P + p.w_off[l] + o * 64;
-      tmem_ld32(base, v);
-      if (o < dout) {
+      float* Pl = P + p.w_off[l] + o * 64 + 32 * half;
+      if (!first) {
+        uint32_t v[32];
+        tmem_ld32(tmem + lane_base + 128 + uint32_t(l * 64 + 32 * half), v);
+        if (o < dout) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q)
-          reinterpret_cast<float4*>(Pl)[q] = make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
-                                                         __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
+          for (int q = 0; q < 8; ++q)
+            reinterpret_cast<float4*>(Pl)[q] = make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
+                                                           __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
+        }
+      } else if (o < dout) {
+        for (int q = 0; q < 8; ++q) reinterpret_cast<float4*>(Pl)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
-      tmem_ld32(base + 32, v);
-      if (o < dout) {
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-          reinterpret_cast<float4*>(Pl + 32)[q] = make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
-                                                              __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
-      }
-    }
-  } else if (first && warp < 2) {
-    for (int l = 0; l < L; ++l) {
-      const int dout = (l + 1 < L) ? 64 : kOutDims;
-      if (tid < dout)
-        for (int i = 0; i < 64; ++i) P[p.w_off[l] + tid * 64 + i] = 0.0f;
     }
   }
   float s = loss_acc;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-  if ((tid & 31) == 0) red[warp] = s;
+  if (half == 0 && (tid & 31) == 0) red[warp] = s;
   fence_before();
   __syncthreads();
-  if (tid == 0) {
-    float tot = 0.0f;
-    for (int k = 0; k < kTrainThreads / 32; ++k) tot += red[k];
-    P[p.n_params] = tot * p.inv3n;
-  }
+  if (tid == 0) P[p.n_params] = ((red[0] + red[1]) + (red[2] + red[3])) * p.inv3n;
   if (warp == 0) {
     fence_after();
     tmem_dealloc(tmem, kTmemCols);

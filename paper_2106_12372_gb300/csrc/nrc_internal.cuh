@@ -6,7 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/nrc.h"
+#include "nrc.h"
 
 namespace nrc {
 
@@ -162,6 +162,34 @@ __device__ __forceinline__ void encode_record(const float* r, float pad, float* 
   for (int j = 0; j < 6; ++j) f[56 + j] = r[8 + j];
   f[62] = pad;
   f[63] = pad;
+}
+
+// Half of the 64 features: half 0 -> features 0..31 (x0 d=0..11, x1 d=0..11,
+// x2 d=0..7); half 1 -> features 32..63 (x2 d=8..11, the five one-blobs, the
+// albedos, the pad).  Same arithmetic as encode_record.
+template <int MODE>
+__device__ __forceinline__ void encode_record_half(const float* r, float pad, int half, float* f) {
+  if (half == 0) {
+#pragma unroll
+    for (int d = 0; d < 12; ++d) {
+      f[d] = (MODE == 0) ? tri_sin(r[0] * float(1 << d)) : sinpif(r[0] * float(1 << d));
+      f[12 + d] = (MODE == 0) ? tri_sin(r[1] * float(1 << d)) : sinpif(r[1] * float(1 << d));
+    }
+#pragma unroll
+    for (int d = 0; d < 8; ++d) f[24 + d] = (MODE == 0) ? tri_sin(r[2] * float(1 << d)) : sinpif(r[2] * float(1 << d));
+  } else {
+#pragma unroll
+    for (int d = 8; d < 12; ++d) f[d - 8] = (MODE == 0) ? tri_sin(r[2] * float(1 << d)) : sinpif(r[2] * float(1 << d));
+    oneblob4<MODE>(r[3], f + 4);
+    oneblob4<MODE>(r[4], f + 8);
+    oneblob4<MODE>(r[5], f + 12);
+    oneblob4<MODE>(r[6], f + 16);
+    oneblob4<MODE>(-expm1f(-r[7]), f + 20);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) f[24 + j] = r[8 + j];
+    f[30] = pad;
+    f[31] = pad;
+  }
 }
 
 __device__ __forceinline__ void load_record(const float* rec, int64_t row, float* r) {
