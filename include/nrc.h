@@ -193,6 +193,39 @@ NRC_API nrc_status nrc_check_error(nrc_cache* cache, nrc_stream stream);
 /* Number of kernels the library launched on this cache since creation. */
 NRC_API int64_t nrc_launch_count(const nrc_cache* cache);
 
+/* Training step that allocates nothing (the paper has no counterpart; this
+ * serves callers that cannot allocate device memory when they train -- e.g.
+ * a renderer whose engine hands out every device allocation itself under a
+ * fixed budget, or a frame loop that must not take the device-wide
+ * synchronisation cudaMalloc / cudaFree can imply).
+ *
+ * Computes exactly what nrc_train_step computes for a cache with config
+ * *cfg (dtype NRC_FP16 or NRC_BF16, width 64, 1..5 hidden layers), on state
+ * the CALLER owns, all device pointers: weights, adam_m, adam_v
+ * (nrc_param_count floats each, layout of nrc_get_state; read and updated
+ * in place) and *step_counter (device int64, incremented).  pool, target,
+ * n_pool, batch (<= 65536), frame_seed, step_in_frame and loss_out as in
+ * nrc_train_step; err_out (device int32, may be NULL) receives the device
+ * error word of this call (0, or NRC's timeout bit 1).
+ *
+ * Scratch lives in file-scope device arrays of fixed size held by every GPU
+ * that loads the library until exit: 64 weight-gradient partials of 20,676
+ * floats (5.3 MB), a 43,008-byte 16-bit weight image and an error word.
+ * Sizes beyond that (other widths, more layers, batch > 65536) are rejected
+ * with NRC_ERR_INVALID_ARG before anything is launched.  No cudaMalloc,
+ * cudaFree or allocating library routine is called.  The first call on each
+ * device looks up the arrays' device addresses with cudaGetSymbolAddress
+ * (with that device current); make that first call before any stream
+ * capture.  Every call shares the arrays: each call rebuilds the weight
+ * image and clears the error word before using them, and calls whose work
+ * overlaps on the GPU (other streams, other threads) race on the scratch and
+ * must be serialised by the caller. */
+NRC_API nrc_status nrc_train_step_noalloc(const nrc_config* cfg, float* weights, float* adam_m, float* adam_v,
+                                          int64_t* step_counter, const float* pool, const float* target,
+                                          int64_t n_pool, int64_t batch, uint64_t frame_seed,
+                                          int32_t step_in_frame, float* loss_out, int32_t* err_out,
+                                          nrc_stream stream);
+
 /* Why the last failing call on this thread failed ("" if none). */
 NRC_API const char* nrc_last_error_string(void);
 

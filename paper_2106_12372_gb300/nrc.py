@@ -86,6 +86,7 @@ def lib() -> ctypes.CDLL:
             "nrc_check_error": (i32, [P, P]),
             "nrc_launch_count": (i64, [P]),
             "nrc_last_error_string": (ctypes.c_char_p, []),
+            "nrc_train_step_noalloc": (i32, [P, P, P, P, P, P, P, i64, i64, u64, i32, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -136,6 +137,15 @@ def gather(pool, target, batch: int, frame_seed: int, step: int, stream=None):
     _check(lib().nrc_gather(_ptr(pool), _ptr(target), pool.shape[0], batch, frame_seed & (2**64 - 1), step,
                             _ptr(rec), _ptr(tgt), _stream(stream)))
     return rec, tgt
+
+
+def train_step_noalloc(cfg: Config, weights, adam_m, adam_v, step_counter, pool, target, batch: int,
+                       frame_seed: int, step: int, loss_out=None, err_out=None, stream=None) -> None:
+    """Allocation-free training step on caller-owned device state (see include/nrc.h)."""
+    _check(lib().nrc_train_step_noalloc(ctypes.byref(cfg), _ptr(weights), _ptr(adam_m), _ptr(adam_v),
+                                        _ptr(step_counter), _ptr(pool), _ptr(target), pool.shape[0], batch,
+                                        frame_seed & (2**64 - 1), step, _ptr(loss_out), _ptr(err_out),
+                                        _stream(stream)))
 
 
 class Cache:
