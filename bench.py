@@ -177,15 +177,18 @@ def run_gpu(args):
 
     cache = nrc.Cache(dtype=args.dtype, seed=seed)
 
+    empty_q = queries[0][:0]
+
     def frame(k, ev=None):
+        # the frame through the C ABI: the cache query (nrc_infer), then the frame's
+        # N_STEPS training steps in one nrc_frame call (no queries)
         q = queries[k % 2]
         if ev:
             ev[0].record(stream)
         cache.infer(q, rgb)
         if ev:
             ev[1].record(stream)
-        for s in range(N_STEPS):
-            cache.train_step(pool, tgt, BATCH, synth.frame_seed(seed, k), s, loss_out=losses[s:s + 1])
+        cache.frame(empty_q, rgb, pool, tgt, BATCH, N_STEPS, synth.frame_seed(seed, k), loss_out=losses)
         if ev:
             ev[2].record(stream)
 
@@ -224,8 +227,7 @@ def run_gpu(args):
         flush.zero_()
         pev[0].record(stream)
         plain.infer(queries[0], rgb)
-        for s in range(N_STEPS):
-            plain.train_step(pool, tgt, BATCH, synth.frame_seed(seed, k), s)
+        plain.frame(empty_q, rgb, pool, tgt, BATCH, N_STEPS, synth.frame_seed(seed, k))
         pev[1].record(stream)
         torch.cuda.synchronize()
         if k > 0:

@@ -402,6 +402,18 @@ cudaError_t launch_train_simt(Cache* c, const float* pool, const float* target, 
 // warp order.  Block 0's warp 1 also sums the loss slots.
 constexpr int kAdamGroups = 8;
 
+// b^t for integer t >= 0 by repeated squaring in FP32: exact for t = 1, about
+// 2 log2(t) roundings otherwise (FP64 arithmetic is slow on this part).
+__device__ __forceinline__ float pow_int(float b, long long t) {
+  float r = 1.0f;
+  while (t > 0) {
+    if (t & 1) r *= b;
+    b *= b;
+    t >>= 1;
+  }
+  return r;
+}
+
 template <int IMG>  // 0: no image, 1: FP16, 2: BF16
 __global__ void __launch_bounds__(32 * kAdamGroups) k_adam(float* __restrict__ w, float* __restrict__ m,
                                                            float* __restrict__ v, const long long* __restrict__ t_ctr,
@@ -413,10 +425,10 @@ __global__ void __launch_bounds__(32 * kAdamGroups) k_adam(float* __restrict__ w
   __shared__ float red[kAdamGroups][32];
   __shared__ float corr[2];
   const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
-  if (threadIdx.x == 0) {  // bias corrections 1 - beta^t, once per block (FP64 is slow on this part)
-    const double t = double(*t_ctr);
-    corr[0] = float(1.0 - pow(double(b1), t));
-    corr[1] = float(1.0 - pow(double(b2), t));
+  if (threadIdx.x == 0) {  // bias corrections 1 - beta^t, once per block
+    const long long t = *t_ctr;
+    corr[0] = 1.0f - pow_int(b1, t);
+    corr[1] = 1.0f - pow_int(b2, t);
   }
   const size_t stride = partial_stride(net.n_params);
   const int p = blockIdx.x * 32 + lane;

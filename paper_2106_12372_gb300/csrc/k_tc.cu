@@ -1,7 +1,7 @@
 // Fused tensor-core (tcgen05) kernels for the neural radiance cache MLP.
 //
 // Inference (Sec. 4, fully fused network; Fig. 4): one persistent CTA per SM
-// with kSlots warpgroups; each warpgroup owns one 128-row batch tile at a
+// with kSlots = 5 warpgroups; each warpgroup owns one 128-row batch tile at a
 // time and a private slice of tensor memory (TMEM):
 //   acc: 64 FP32 columns, the MMA accumulator D (row = TMEM lane);
 //   act: 32 columns holding the tile's 64 activations as packed 16-bit pairs,
@@ -23,10 +23,10 @@
 namespace nrc {
 using namespace tc;
 
-constexpr int kSlots = 4;
+constexpr int kSlots = 5;  // 5 x (64 + 32) = 480 of the 512 TMEM columns
 constexpr int kInferThreads = 128 * kSlots;
 constexpr int kTmemCols = 512;
-constexpr int kSlotCols = 128;
+constexpr int kSlotCols = 96;
 
 struct InferParams {
   const float* rec;
@@ -144,7 +144,9 @@ __global__ void __launch_bounds__(kInferThreads, 1) k_infer_tc(const __grid_cons
                  idesc, k > 0 ? 1u : 0u);
         mma_commit(&bar_mma[slot]);
       }
-      mbar_wait(&bar_mma[slot], phase, p.err);
+      // one thread waits for the MMAs; the rest of the warpgroup sleeps at the barrier
+      if (rit == 0) mbar_wait(&bar_mma[slot], phase, p.err);
+      named_sync(1 + slot, 128);
       phase ^= 1u;
       fence_after();
       if (l + 1 < p.n_mats) {
@@ -179,9 +181,15 @@ __global__ void __launch_bounds__(kInferThreads, 1) k_infer_tc(const __grid_cons
   }
 }
 
+// Raises a kernel's dynamic shared-memory limit once per process (the
+// attribute is per function; repeating the call on every launch costs
+// host time on the launch path).  `done` is per kernel instance.
 template <typename K>
-static cudaError_t set_smem(K kernel, int bytes) {
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+static cudaError_t set_smem(K kernel, int bytes, int* done) {
+  if (*done >= bytes) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) *done = bytes;
+  return e;
 }
 
 cudaError_t launch_infer_tc(Cache* c, const float* rec, int64_t n, float* rgb, cudaStream_t st) {
@@ -202,9 +210,10 @@ cudaError_t launch_infer_tc(Cache* c, const float* rec, int64_t n, float* rgb, c
   const bool bf16 = c->cfg.dtype == NRC_BF16;
   const int mode = c->cfg.enc_mode;
   cudaError_t e;
-#define NRC_LAUNCH(M, B)                                          \
-  e = set_smem(k_infer_tc<M, B>, smem);                           \
-  if (e != cudaSuccess) return e;                                 \
+  static int attr_done[4] = {0, 0, 0, 0};
+#define NRC_LAUNCH(M, B)                                                   \
+  e = set_smem(k_infer_tc<M, B>, smem, &attr_done[2 * (M) + ((B) ? 1 : 0)]); \
+  if (e != cudaSuccess) return e;                                          \
   k_infer_tc<M, B><<<grid, kInferThreads, smem, st>>>(p);
   if (mode == 0 && !bf16) {
     NRC_LAUNCH(0, false)
@@ -483,28 +492,33 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(const __grid_cons
   if (!have_w) mbar_wait(&bar_w, 0, p.err);  // never leave with the weight copy in flight
 
   // ------------------------------------------------- write this CTA's partial
+  // dW_l sits in TMEM lanes 0..63 (row o), columns 32h.. (warps 0, 1, 4, 5).
+  // It is transposed through shared memory (rows padded to 65 floats: both
+  // the row-wise writes and the column-wise reads are free of bank
+  // conflicts) so that the global stores of all 256 threads are coalesced.
+  // The staging buffers reuse the activation area, idle after the backward pass.
   fence_before();
   __syncthreads();
   fence_after();
   float* P = p.partials + size_t(blockIdx.x) * partial_stride(p.n_params);
-  if ((warp & 3) < 2) {  // dW rows o = TMEM lanes 0..63; this thread writes columns 32h .. 32h+31
-    const int o = r;
-    for (int l = 0; l < L; ++l) {
-      const int dout = (l + 1 < L) ? 64 : kOutDims;
-      float* Pl = P + p.w_off[l] + o * 64 + 32 * half;
+  for (int l = 0; l < L; ++l) {
+    const int dout = (l + 1 < L) ? 64 : kOutDims;
+    float* S = reinterpret_cast<float*>(Hs) + (l & 1) * (64 * 65);
+    if ((warp & 3) < 2) {
+      const int o = r;
       if (!first) {
         uint32_t v[32];
         tmem_ld32(tmem + lane_base + 128 + uint32_t(l * 64 + 32 * half), v);
-        if (o < dout) {
 #pragma unroll
-          for (int q = 0; q < 8; ++q)
-            reinterpret_cast<float4*>(Pl)[q] = make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
-                                                           __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
-        }
-      } else if (o < dout) {
-        for (int q = 0; q < 8; ++q) reinterpret_cast<float4*>(Pl)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int c = 0; c < 32; ++c) S[o * 65 + 32 * half + c] = __uint_as_float(v[c]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) S[o * 65 + 32 * half + c] = 0.0f;
       }
     }
+    __syncthreads();
+    float* Pl = P + p.w_off[l];
+    for (int e = tid; e < dout * 64; e += kTrainThreads) Pl[e] = S[(e >> 6) * 65 + (e & 63)];
   }
   float s = loss_acc;
 #pragma unroll
@@ -550,9 +564,10 @@ cudaError_t launch_train_tc(Cache* c, const float* pool, const float* target, in
   const int smem = ((p.img_bytes + 1023) & ~1023) + p.n_mats * 16384 + 16384 + 1024;
   const bool bf16 = c->cfg.dtype == NRC_BF16;
   const int mode = c->cfg.enc_mode;
-#define NRC_LAUNCH(M, B)                                          \
-  e = set_smem(k_train_tc<M, B>, smem);                           \
-  if (e != cudaSuccess) return e;                                 \
+  static int attr_done[4] = {0, 0, 0, 0};
+#define NRC_LAUNCH(M, B)                                                   \
+  e = set_smem(k_train_tc<M, B>, smem, &attr_done[2 * (M) + ((B) ? 1 : 0)]); \
+  if (e != cudaSuccess) return e;                                          \
   k_train_tc<M, B><<<grid, kTrainThreads, smem, st>>>(p);
   if (mode == 0 && !bf16) {
     NRC_LAUNCH(0, false)
