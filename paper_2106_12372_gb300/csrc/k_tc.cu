@@ -356,7 +356,10 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(const __grid_cons
   const int64_t n_tiles = (p.batch + kTile - 1) / kTile;
   bool first = true;
 
-  auto mma_sync_issue_wait = [&](auto&& issue) {
+  // One dependent step: make this warpgroup pair's shared-memory and TMEM
+  // writes visible, issue the MMAs (one thread), run `overlap` while they
+  // execute, wait for them.
+  auto mma_stage = [&](auto&& issue, auto&& overlap) {
     fence_proxy_async_smem();
     fence_before();
     named_sync(1, kTrainThreads);
@@ -365,9 +368,43 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(const __grid_cons
       issue();
       mma_commit(&bar_mma);
     }
+    overlap();
     mbar_wait(&bar_mma, phase, p.err);
     phase ^= 1u;
     fence_after();
+  };
+  auto mma_sync_issue_wait = [&](auto&& issue) { mma_stage(issue, []() {}); };
+
+  // Weight-gradient write-out, overlapped with the backward pass of the CTA's
+  // last tile: once dW_l is final and H_l is no longer needed, the threads
+  // owning TMEM lanes 0..63 stage dW_l into H_l's buffer (row o at o*64 floats,
+  // 16-byte chunk c of each 128-byte half at chunk c ^ (o % 8): conflict-free),
+  // and after the next barrier all 256 threads copy it to the CTA's partial
+  // with coalesced stores.
+  float* P = p.partials + size_t(blockIdx.x) * partial_stride(p.n_params);
+  auto stage_dw = [&](int l) {
+    if ((warp & 3) >= 2) return;
+    const int o = r;
+    const int dout = (l + 1 < L) ? 64 : kOutDims;
+    uint32_t v[32];
+    tmem_ld32(tmem + lane_base + 128 + uint32_t(l * 64 + 32 * half), v);
+    if (o < dout) {
+      float* seg = reinterpret_cast<float*>(Hs + l * 16384) + o * 64 + 32 * half;
+#pragma unroll
+      for (int c = 0; c < 8; ++c)
+        *reinterpret_cast<float4*>(seg + ((c ^ (o & 7)) << 2)) =
+            make_float4(__uint_as_float(v[4 * c]), __uint_as_float(v[4 * c + 1]), __uint_as_float(v[4 * c + 2]),
+                        __uint_as_float(v[4 * c + 3]));
+    }
+  };
+  auto write_dw = [&](int l) {
+    const int dout = (l + 1 < L) ? 64 : kOutDims;
+    const float* S = reinterpret_cast<const float*>(Hs + l * 16384);
+    float* Pl = P + p.w_off[l];
+    for (int e = tid; e < dout * 64; e += kTrainThreads) {
+      const int o = e >> 6, i = e & 63;
+      Pl[e] = S[o * 64 + (i & 32) + ((((i >> 2) & 7) ^ (o & 7)) << 2) + (i & 3)];
+    }
   };
 
   for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
@@ -454,9 +491,10 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(const __grid_cons
     tmem_st_wait();
 
     // ----------------------------------------------------------- backward
+    const bool last_tile = tile + int64_t(gridDim.x) >= n_tiles;
     for (int l = L - 1; l >= 0; --l) {
       const bool first_acc = first;
-      mma_sync_issue_wait([&]() {
+      mma_stage([&]() {
         // dW_l (+)= delta_{l+1}^T H_l over this tile's 128 rows
         const uint32_t idw = idesc_f16(128, 64, BF16, true, true);
         const uint32_t dcol = tmem + 128 + uint32_t(l * 64);
@@ -473,6 +511,11 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(const __grid_cons
           for (int k = 0; k < K / 16; ++k)
             mma_ts(tmem + 0, tmem + 64 + uint32_t(k * 8), sdesc_sw128(b0 + uint32_t(k * 2048), 1024, 1024), idd,
                    k > 0 ? 1u : 0u);
+        }
+      }, [&]() {
+        if (last_tile) {
+          if (l + 1 < L) stage_dw(l + 1);  // dW_{l+1} final since the previous stage; its mask read is done
+          if (l + 2 < L) write_dw(l + 2);  // staged during the previous stage, before this stage's barrier
         }
       });
       if (l == 0) break;
@@ -491,34 +534,14 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(const __grid_cons
 
   if (!have_w) mbar_wait(&bar_w, 0, p.err);  // never leave with the weight copy in flight
 
-  // ------------------------------------------------- write this CTA's partial
-  // dW_l sits in TMEM lanes 0..63 (row o), columns 32h.. (warps 0, 1, 4, 5).
-  // It is transposed through shared memory (rows padded to 65 floats: both
-  // the row-wise writes and the column-wise reads are free of bank
-  // conflicts) so that the global stores of all 256 threads are coalesced.
-  // The staging buffers reuse the activation area, idle after the backward pass.
-  fence_before();
-  __syncthreads();
-  fence_after();
-  float* P = p.partials + size_t(blockIdx.x) * partial_stride(p.n_params);
-  for (int l = 0; l < L; ++l) {
-    const int dout = (l + 1 < L) ? 64 : kOutDims;
-    float* S = reinterpret_cast<float*>(Hs) + (l & 1) * (64 * 65);
-    if ((warp & 3) < 2) {
-      const int o = r;
-      if (!first) {
-        uint32_t v[32];
-        tmem_ld32(tmem + lane_base + 128 + uint32_t(l * 64 + 32 * half), v);
-#pragma unroll
-        for (int c = 0; c < 32; ++c) S[o * 65 + 32 * half + c] = __uint_as_float(v[c]);
-      } else {
-#pragma unroll
-        for (int c = 0; c < 32; ++c) S[o * 65 + 32 * half + c] = 0.0f;
-      }
-    }
+  // ------------------------------------------- the rest of the CTA's partial
+  if (!first) {
+    stage_dw(0);  // dW_0 is final after the last backward stage (no epilogue reads H_0 there)
     __syncthreads();
-    float* Pl = P + p.w_off[l];
-    for (int e = tid; e < dout * 64; e += kTrainThreads) Pl[e] = S[(e >> 6) * 65 + (e & 63)];
+    if (L >= 2) write_dw(1);
+    write_dw(0);
+  } else {  // a CTA without a tile contributes zeros
+    for (int e = tid; e < p.n_params; e += kTrainThreads) P[e] = 0.0f;
   }
   float s = loss_acc;
 #pragma unroll
