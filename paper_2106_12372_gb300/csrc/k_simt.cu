@@ -425,6 +425,8 @@ __global__ void __launch_bounds__(32 * kAdamGroups) k_adam(float* __restrict__ w
   __shared__ float red[kAdamGroups][32];
   __shared__ float corr[2];
   const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+  pdl_wait();  // the partials and the step counter come from the kernel before
+  pdl_launch_dependents();
   if (threadIdx.x == 0) {  // bias corrections 1 - beta^t, once per block
     const long long t = *t_ctr;
     corr[0] = 1.0f - pow_int(b1, t);
@@ -484,16 +486,27 @@ cudaError_t launch_adam(Cache* c, int n_partials, float grad_scale, float* loss_
   const int threads = 32 * kAdamGroups;
   const int blocks = (c->net.n_params + 31) / 32;
   const nrc_config& k = c->cfg;
+  // Launched with programmatic stream serialisation: its blocks may start
+  // before the gradient kernel finishes and wait for it on the device.
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3(unsigned(blocks));
+  lc.blockDim = dim3(unsigned(threads));
+  lc.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  lc.attrs = attr;
+  lc.numAttrs = 1;
+  const NetShape& net = c->net;
+  const ImageShape& img = c->img;
   if (k.dtype == NRC_FP16)
-    k_adam<1><<<blocks, threads, 0, st>>>(c->w, c->m, c->v, c->t, c->partials, n_partials, c->net, c->img, c->wimg,
-                                          grad_scale, k.lr, k.beta1, k.beta2, k.adam_eps, loss_out);
-  else if (k.dtype == NRC_BF16)
-    k_adam<2><<<blocks, threads, 0, st>>>(c->w, c->m, c->v, c->t, c->partials, n_partials, c->net, c->img, c->wimg,
-                                          grad_scale, k.lr, k.beta1, k.beta2, k.adam_eps, loss_out);
-  else
-    k_adam<0><<<blocks, threads, 0, st>>>(c->w, c->m, c->v, c->t, c->partials, n_partials, c->net, c->img, c->wimg,
-                                          grad_scale, k.lr, k.beta1, k.beta2, k.adam_eps, loss_out);
-  return cudaGetLastError();
+    return cudaLaunchKernelEx(&lc, k_adam<1>, c->w, c->m, c->v, (const long long*)c->t, (const float*)c->partials,
+                              n_partials, net, img, c->wimg, grad_scale, k.lr, k.beta1, k.beta2, k.adam_eps, loss_out);
+  if (k.dtype == NRC_BF16)
+    return cudaLaunchKernelEx(&lc, k_adam<2>, c->w, c->m, c->v, (const long long*)c->t, (const float*)c->partials,
+                              n_partials, net, img, c->wimg, grad_scale, k.lr, k.beta1, k.beta2, k.adam_eps, loss_out);
+  return cudaLaunchKernelEx(&lc, k_adam<0>, c->w, c->m, c->v, (const long long*)c->t, (const float*)c->partials,
+                            n_partials, net, img, c->wimg, grad_scale, k.lr, k.beta1, k.beta2, k.adam_eps, loss_out);
 }
 
 __global__ void k_step_increment(long long* t) { *t += 1; }

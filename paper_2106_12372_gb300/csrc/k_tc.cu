@@ -334,17 +334,13 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(const __grid_cons
     mbar_init(&bar_w, 1);
     mbar_init(&bar_mma, 1);
     fence_barrier_init();
-    if (blockIdx.x == 0) *p.t_ctr += 1;  // Adam's step counter for the update that follows
   }
   fence_before();
   __syncthreads();
   fence_after();
+  pdl_launch_dependents();  // the Adam kernel that follows may be scheduled now; it waits for this grid
   const uint32_t tmem = tmem_base_sh;
-  if (tid == 0) {
-    mbar_arrive_expect_tx(&bar_w, uint32_t(p.img_bytes));
-    bulk_g2s(sw, p.wimg, uint32_t(p.img_bytes), &bar_w);
-  }
-  bool have_w = false;  // the weight copy is waited for before the first MMA
+  bool have_w = false;  // the weights are requested after the first tile's gather and encoding
 
   const uint32_t lane_base = uint32_t((warp & 3) * 32) << 16;
   const uint32_t t_acc = tmem + lane_base + uint32_t(32 * half);        // my 32 accumulator columns
@@ -435,6 +431,15 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(const __grid_cons
     tmem_st16(t_act, pk);
     tmem_st_wait();
     if (!have_w) {
+      // Everything above reads only this step's inputs, so it may overlap the
+      // previous step's Adam kernel; the weights, the step counter and the
+      // partials belong to that step and are touched only after it completes.
+      pdl_wait();
+      if (tid == 0) {
+        if (blockIdx.x == 0) *p.t_ctr += 1;  // Adam's step counter for the update that follows
+        mbar_arrive_expect_tx(&bar_w, uint32_t(p.img_bytes));
+        bulk_g2s(sw, p.wimg, uint32_t(p.img_bytes), &bar_w);
+      }
       mbar_wait(&bar_w, 0, p.err);
       have_w = true;
     }
@@ -532,7 +537,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(const __grid_cons
     first = false;
   }
 
-  if (!have_w) mbar_wait(&bar_w, 0, p.err);  // never leave with the weight copy in flight
+  if (!have_w) pdl_wait();  // (a CTA without a tile still orders its partial after the predecessor)
 
   // ------------------------------------------- the rest of the CTA's partial
   if (!first) {
@@ -588,10 +593,21 @@ cudaError_t launch_train_tc(Cache* c, const float* pool, const float* target, in
   const bool bf16 = c->cfg.dtype == NRC_BF16;
   const int mode = c->cfg.enc_mode;
   static int attr_done[4] = {0, 0, 0, 0};
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3(unsigned(grid));
+  lc.blockDim = dim3(kTrainThreads);
+  lc.dynamicSmemBytes = size_t(smem);
+  lc.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  lc.attrs = attr;
+  lc.numAttrs = 1;
 #define NRC_LAUNCH(M, B)                                                   \
   e = set_smem(k_train_tc<M, B>, smem, &attr_done[2 * (M) + ((B) ? 1 : 0)]); \
   if (e != cudaSuccess) return e;                                          \
-  k_train_tc<M, B><<<grid, kTrainThreads, smem, st>>>(p);
+  e = cudaLaunchKernelEx(&lc, k_train_tc<M, B>, p);                        \
+  if (e != cudaSuccess) return e;
   if (mode == 0 && !bf16) {
     NRC_LAUNCH(0, false)
   } else if (mode == 0 && bf16) {

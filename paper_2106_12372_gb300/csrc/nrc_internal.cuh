@@ -210,6 +210,13 @@ __host__ __device__ __forceinline__ uint32_t sw128_offset(uint32_t n, uint32_t k
   return (n >> 3) * 1024u + (n & 7u) * 128u + ((((k >> 3) ^ n) & 7u) << 4) + (k & 7u) * 2u;
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation may start while its predecessor in the stream still runs;
+// pdl_wait() blocks until the predecessor has completed and its writes are
+// visible, pdl_launch_dependents() lets the successor start early.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
