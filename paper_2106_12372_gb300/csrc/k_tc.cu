@@ -150,14 +150,13 @@ __global__ void __launch_bounds__(kInferThreads, 1) k_infer_tc(const __grid_cons
       phase ^= 1u;
       fence_after();
       if (l + 1 < p.n_mats) {
-        uint32_t v[32];
-        tmem_ld32(t_acc, v);
+        uint32_t v[64];
+        tmem_ld64(t_acc, v);
 #pragma unroll
         for (int j = 0; j < 16; ++j) pk[j] = pack2<BF16, true>(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
         tmem_st16(t_act, pk);
-        tmem_ld32(t_acc + 32, v);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) pk[j] = pack2<BF16, true>(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
+        for (int j = 0; j < 16; ++j) pk[j] = pack2<BF16, true>(__uint_as_float(v[32 + 2 * j]), __uint_as_float(v[33 + 2 * j]));
         tmem_st16(t_act + 16, pk);
         tmem_st_wait();
       } else {

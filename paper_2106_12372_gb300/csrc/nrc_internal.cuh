@@ -149,8 +149,13 @@ __device__ __forceinline__ void encode_record(const float* r, float pad, float* 
   for (int j = 0; j < 3; ++j) {
 #pragma unroll
     for (int d = 0; d < 12; ++d) {
-      const float y = r[j] * float(1 << d);  // exact
-      f[12 * j + d] = (MODE == 0) ? tri_sin(y) : sinpif(y);
+      if (MODE == 0) {
+        // tri(2^d x - 1/2) = |4 frac(2^(d-1) x - 1/4) - 2| - 1; 2^(d-1) x is exact
+        const float t = fmaf(r[j], float(1 << d) * 0.5f, -0.25f);
+        f[12 * j + d] = fabsf(fmaf(4.0f, t - floorf(t), -2.0f)) - 1.0f;
+      } else {
+        f[12 * j + d] = sinpif(r[j] * float(1 << d));
+      }
     }
   }
   oneblob4<MODE>(r[3], f + 36);
