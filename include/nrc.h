@@ -193,6 +193,53 @@ NRC_API nrc_status nrc_check_error(nrc_cache* cache, nrc_stream stream);
 /* Number of kernels the library launched on this cache since creation. */
 NRC_API int64_t nrc_launch_count(const nrc_cache* cache);
 
+/* ----------------------------------------------------------------------
+ * Batched caches: several independent caches (each with its own weights,
+ * Adam state and training data) served together.  All caches of a batch must
+ * have been created with identical configurations (FP16 or BF16), on the
+ * same device.  The batch object owns its descriptors and the weight-gradient
+ * partials of batched training steps; the caches stay owned by the caller.
+ */
+typedef struct nrc_batch nrc_batch;
+
+/* Plans batched calls over caches[0 .. n_caches-1] (host array of handles). */
+NRC_API nrc_status nrc_batch_create(nrc_cache* const* caches, int32_t n_caches, nrc_batch** out);
+
+/* Frees the batch (not the caches) after synchronising the device. */
+NRC_API nrc_status nrc_batch_destroy(nrc_batch* batch);
+
+/* Cache queries of every cache in ONE persistent launch (Sec. 4's fused
+ * network per cache): rgb[c][n[c]][3] = MLP_c(encode(records[c][n[c]][16])).
+ * records, n and rgb are host arrays of n_caches entries; records[c] and
+ * rgb[c] are device pointers as in nrc_infer.  The work is cut into units of
+ * up to unit_tiles 128-row tiles of one cache, taken by the CTAs from a
+ * device counter; each row is computed exactly as nrc_infer computes it.
+ * Descriptors are uploaded (asynchronously) only when they differ from the
+ * previous call's, so the launch can be captured in a CUDA graph and
+ * replayed for the same buffers. */
+NRC_API nrc_status nrc_batch_infer(nrc_batch* batch, const float* const* records, const int64_t* n,
+                                   float* const* rgb, nrc_stream stream);
+
+/* One training step of every cache in one gradient launch and one Adam
+ * launch: cache c trains on batch `step` of frame_seed[c]'s shuffle of its
+ * pool (as nrc_train_step), batch[c] <= 65536 records (0 skips the cache).
+ * The CTAs are shared out in proportion to the caches' batches.  All
+ * arguments are host arrays of n_caches entries; pool[c], target[c] and
+ * loss_out[c] (may be NULL, as may loss_out itself) are device pointers. */
+NRC_API nrc_status nrc_batch_train_step(nrc_batch* batch, const float* const* pool, const float* const* target,
+                                        const int64_t* n_pool, const int64_t* batch_size,
+                                        const uint64_t* frame_seed, int32_t step, float* const* loss_out,
+                                        nrc_stream stream);
+
+/* Sets the work-unit size of nrc_batch_infer (1 .. 4096 tiles; default 20). */
+NRC_API nrc_status nrc_batch_set_unit_tiles(nrc_batch* batch, int32_t unit_tiles);
+
+/* Autotuner: runs nrc_batch_infer on the given buffers with each candidate
+ * work-unit size (5 .. 160 tiles), keeps the fastest (CUDA-event timing; it
+ * synchronises the stream) and reports it in *chosen (may be NULL). */
+NRC_API nrc_status nrc_batch_autotune(nrc_batch* batch, const float* const* records, const int64_t* n,
+                                      float* const* rgb, nrc_stream stream, int32_t* chosen);
+
 /* Training step that allocates nothing (the paper has no counterpart; this
  * serves callers that cannot allocate device memory when they train -- e.g.
  * a renderer whose engine hands out every device allocation itself under a

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnrc.so")
-SOURCES = ["nrc_api.cu", "k_simt.cu", "k_tc.cu", "k_plain.cu", "nrc_noalloc.cu"]
+SOURCES = ["nrc_api.cu", "k_simt.cu", "k_tc.cu", "k_plain.cu", "nrc_noalloc.cu", "nrc_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -414,19 +414,16 @@ __device__ __forceinline__ float pow_int(float b, long long t) {
   return r;
 }
 
+// One block: the 32 weights p = blockIdx.x * 32 + lane of one cache.
 template <int IMG>  // 0: no image, 1: FP16, 2: BF16
-__global__ void __launch_bounds__(32 * kAdamGroups) k_adam(float* __restrict__ w, float* __restrict__ m,
-                                                           float* __restrict__ v, const long long* __restrict__ t_ctr,
-                                                           const float* __restrict__ partials, int n_partials,
-                                                           const __grid_constant__ NetShape net,
-                                                           const __grid_constant__ ImageShape img,
-                                                           uint8_t* __restrict__ wimg, float grad_scale, float lr,
-                                                           float b1, float b2, float eps, float* __restrict__ loss_out) {
+__device__ __forceinline__ void adam_block(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
+                                           const long long* __restrict__ t_ctr, const float* __restrict__ partials,
+                                           int n_partials, const NetShape& net, const ImageShape& img,
+                                           uint8_t* __restrict__ wimg, float grad_scale, float lr, float b1, float b2,
+                                           float eps, float* __restrict__ loss_out, bool do_loss) {
   __shared__ float red[kAdamGroups][32];
   __shared__ float corr[2];
   const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
-  pdl_wait();  // the partials and the step counter come from the kernel before
-  pdl_launch_dependents();
   if (threadIdx.x == 0) {  // bias corrections 1 - beta^t, once per block
     const long long t = *t_ctr;
     corr[0] = 1.0f - pow_int(b1, t);
@@ -434,7 +431,7 @@ __global__ void __launch_bounds__(32 * kAdamGroups) k_adam(float* __restrict__ w
   }
   const size_t stride = partial_stride(net.n_params);
   const int p = blockIdx.x * 32 + lane;
-  if (blockIdx.x == 0 && grp == 1 && loss_out) {
+  if (do_loss && grp == 1 && loss_out) {
     float s = 0.0f;
     for (int k = lane; k < n_partials; k += 32) s += partials[size_t(k) * stride + net.n_params];
 #pragma unroll
@@ -482,6 +479,33 @@ __global__ void __launch_bounds__(32 * kAdamGroups) k_adam(float* __restrict__ w
   }
 }
 
+template <int IMG>  // 0: no image, 1: FP16, 2: BF16
+__global__ void __launch_bounds__(32 * kAdamGroups) k_adam(float* __restrict__ w, float* __restrict__ m,
+                                                           float* __restrict__ v, const long long* __restrict__ t_ctr,
+                                                           const float* __restrict__ partials, int n_partials,
+                                                           const __grid_constant__ NetShape net,
+                                                           const __grid_constant__ ImageShape img,
+                                                           uint8_t* __restrict__ wimg, float grad_scale, float lr,
+                                                           float b1, float b2, float eps, float* __restrict__ loss_out) {
+  pdl_wait();  // the partials and the step counter come from the kernel before
+  pdl_launch_dependents();
+  adam_block<IMG>(w, m, v, t_ctr, partials, n_partials, net, img, wimg, grad_scale, lr, b1, b2, eps, loss_out,
+                  blockIdx.x == 0);
+}
+
+// All caches of a batched step: blockIdx.y selects the cache.
+template <int IMG>
+__global__ void __launch_bounds__(32 * kAdamGroups) k_adam_batched(const AdamJob* __restrict__ jobs,
+                                                                   const __grid_constant__ NetShape net,
+                                                                   const __grid_constant__ ImageShape img, float lr,
+                                                                   float b1, float b2, float eps) {
+  pdl_wait();
+  pdl_launch_dependents();
+  const AdamJob J = jobs[blockIdx.y];
+  adam_block<IMG>(J.w, J.m, J.v, J.t_ctr, J.partials, J.n_partials, net, img, J.wimg, J.grad_scale, lr, b1, b2, eps,
+                  J.loss_out, blockIdx.x == 0);
+}
+
 cudaError_t launch_adam(Cache* c, int n_partials, float grad_scale, float* loss_out, cudaStream_t st) {
   const int threads = 32 * kAdamGroups;
   const int blocks = (c->net.n_params + 31) / 32;
@@ -507,6 +531,22 @@ cudaError_t launch_adam(Cache* c, int n_partials, float grad_scale, float* loss_
                               n_partials, net, img, c->wimg, grad_scale, k.lr, k.beta1, k.beta2, k.adam_eps, loss_out);
   return cudaLaunchKernelEx(&lc, k_adam<0>, c->w, c->m, c->v, (const long long*)c->t, (const float*)c->partials,
                             n_partials, net, img, c->wimg, grad_scale, k.lr, k.beta1, k.beta2, k.adam_eps, loss_out);
+}
+
+cudaError_t launch_adam_batched(const Cache* proto, const AdamJob* jobs, int n_jobs, cudaStream_t st) {
+  const nrc_config& k = proto->cfg;
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3(unsigned((proto->net.n_params + 31) / 32), unsigned(n_jobs));
+  lc.blockDim = dim3(32 * kAdamGroups);
+  lc.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  lc.attrs = attr;
+  lc.numAttrs = 1;
+  if (k.dtype == NRC_FP16) return cudaLaunchKernelEx(&lc, k_adam_batched<1>, jobs, proto->net, proto->img, k.lr, k.beta1, k.beta2, k.adam_eps);
+  if (k.dtype == NRC_BF16) return cudaLaunchKernelEx(&lc, k_adam_batched<2>, jobs, proto->net, proto->img, k.lr, k.beta1, k.beta2, k.adam_eps);
+  return cudaLaunchKernelEx(&lc, k_adam_batched<0>, jobs, proto->net, proto->img, k.lr, k.beta1, k.beta2, k.adam_eps);
 }
 
 __global__ void k_step_increment(long long* t) { *t += 1; }

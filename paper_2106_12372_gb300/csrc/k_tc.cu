@@ -18,6 +18,8 @@
 // bit and writes the next layer's A back into TMEM.  The output layer
 // (N = 16, 3 used) is read back and stored as RGB.  Activations never leave
 // the SM.
+#include <cstring>
+
 #include "tc_ptx.cuh"
 
 namespace nrc {
@@ -40,10 +42,120 @@ struct InferParams {
   int* err;
 };
 
+struct BatchInferParams {
+  const BatchCache* caches;
+  const BatchUnit* units;
+  int n_units;
+  unsigned* counter;  // work-unit counter, zero at launch
+  int img_bytes;
+  int n_mats;
+  ImageShape img;
+  float pad;
+  int* err;
+};
+
 __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
   const uint32_t a = smem_u32(p);
   return p + ((1024u - (a & 1023u)) & 1023u);
 }
+
+// Encodes a record (Table 1, Sec. 3.6) and stores the 64 packed 16-bit
+// inputs into the slot's activation columns (this thread's TMEM lane).
+template <int MODE, bool BF16>
+__device__ __forceinline__ void encode_to_tmem(const float (&r)[kRecFloats], float pad, uint32_t t_act) {
+  uint32_t pk[16];
+  float f[kEncDims];
+  encode_record<MODE>(r, pad, f);
+#pragma unroll
+  for (int j = 0; j < 16; ++j) pk[j] = pack2<BF16, false>(f[2 * j], f[2 * j + 1]);
+  tmem_st16(t_act, pk);
+#pragma unroll
+  for (int j = 0; j < 16; ++j) pk[j] = pack2<BF16, false>(f[32 + 2 * j], f[33 + 2 * j]);
+  tmem_st16(t_act + 16, pk);
+  tmem_st_wait();
+}
+
+// The layer chain of one tile in one slot (see the file comment): per layer,
+// the warpgroup's barrier, 4 MMAs issued by one thread, one waiter, and the
+// ReLU + 16-bit epilogue back into the activation columns; the output
+// layer's first 3 columns go to out (this thread's row; null if the row is
+// past the end).
+struct SlotTmem {
+  uint32_t tmem;     // TMEM base (lane 0) of the CTA
+  uint32_t acc_col;  // first accumulator column of the slot
+  uint32_t act_col;  // first activation column of the slot
+  uint32_t t_acc;    // this warp's lanes, accumulator columns
+  uint32_t t_act;    // this warp's lanes, activation columns
+};
+
+template <bool BF16>
+__device__ __forceinline__ void tile_layers(const ImageShape& img, int n_mats, const SlotTmem& st, uint32_t sw_base,
+                                            int slot, int rit, uint64_t* bar, uint32_t& phase, int* err, float* out) {
+  for (int l = 0; l < n_mats; ++l) {
+    fence_before();
+    named_sync(1 + slot, 128);
+    if (rit == 0) {
+      fence_after();
+      const uint32_t idesc = idesc_f16(128, img.rows[l], BF16);
+      const uint32_t b0 = sw_base + uint32_t(img.off[l]);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        mma_ts(st.tmem + st.acc_col, st.tmem + st.act_col + uint32_t(k * 8),
+               sdesc_sw128(b0 + uint32_t(k * 32), 16, 1024), idesc, k > 0 ? 1u : 0u);
+      mma_commit(bar);
+    }
+    // one thread waits for the MMAs; the rest of the warpgroup sleeps at the barrier
+    if (rit == 0) mbar_wait(bar, phase, err);
+    named_sync(1 + slot, 128);
+    phase ^= 1u;
+    fence_after();
+    if (l + 1 < n_mats) {
+      uint32_t v[64], pk[16];
+      tmem_ld64(st.t_acc, v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) pk[j] = pack2<BF16, true>(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
+      tmem_st16(st.t_act, pk);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) pk[j] = pack2<BF16, true>(__uint_as_float(v[32 + 2 * j]), __uint_as_float(v[33 + 2 * j]));
+      tmem_st16(st.t_act + 16, pk);
+      tmem_st_wait();
+    } else {
+      uint32_t v[4];
+      tmem_ld4(st.t_acc, v);
+      if (out) {
+        out[0] = __uint_as_float(v[0]);
+        out[1] = __uint_as_float(v[1]);
+        out[2] = __uint_as_float(v[2]);
+      }
+    }
+  }
+}
+
+// A slot's record staging: two 8 KB buffers of 128 rows x 64 B in shared
+// memory, filled with cp.async; 16-byte chunk q of row r sits at chunk
+// q ^ ((r / 2) % 4) so that the row reads are free of bank conflicts.
+struct RecStage {
+  uint32_t row0;     // shared address of this thread's row in buffer 0
+  const uint8_t* p;  // the same, generic
+  uint32_t rot;
+  __device__ __forceinline__ void fetch(const float* rec, int64_t row, bool ok, int b) const {
+    const float* src = rec + (ok ? row : 0) * kRecFloats;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      cp_async16(row0 + uint32_t(b * 8192) + ((uint32_t(q) ^ rot) << 4), src + 4 * q, ok ? 16u : 0u);
+    cp_async_commit();
+  }
+  __device__ __forceinline__ void read(int b, float (&r)[kRecFloats]) const {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float4 v = *reinterpret_cast<const float4*>(p + b * 8192 + ((uint32_t(q) ^ rot) << 4));
+      r[4 * q] = v.x;
+      r[4 * q + 1] = v.y;
+      r[4 * q + 2] = v.z;
+      r[4 * q + 3] = v.w;
+    }
+  }
+};
 
 template <int MODE, bool BF16>
 __global__ void __launch_bounds__(kInferThreads, 1) k_infer_tc(const __grid_constant__ InferParams p) {
@@ -77,24 +189,22 @@ __global__ void __launch_bounds__(kInferThreads, 1) k_infer_tc(const __grid_cons
   }
 
   const uint32_t lane_base = uint32_t((warp & 3) * 32) << 16;
-  const uint32_t acc_col = uint32_t(slot * kSlotCols);
-  const uint32_t act_col = acc_col + 64;
-  const uint32_t t_acc = tmem + lane_base + acc_col;
-  const uint32_t t_act = tmem + lane_base + act_col;
+  SlotTmem st;
+  st.tmem = tmem;
+  st.acc_col = uint32_t(slot * kSlotCols);
+  st.act_col = st.acc_col + 64;
+  st.t_acc = tmem + lane_base + st.acc_col;
+  st.t_act = tmem + lane_base + st.act_col;
   const uint32_t sw_base = smem_u32(sw);
   const int64_t n_tiles = (p.n + kTile - 1) / kTile;
   const int64_t stride = int64_t(gridDim.x) * kSlots;
-  // this thread's record row in each of the slot's two staging buffers
-  const uint32_t rec_row0 = smem_u32(recs) + uint32_t(slot * 2 * 8192 + rit * 64);
-  const uint32_t rot = uint32_t((rit >> 1) & 3);
+  RecStage rs;
+  rs.row0 = smem_u32(recs) + uint32_t(slot * 2 * 8192 + rit * 64);
+  rs.p = recs + slot * 2 * 8192 + rit * 64;
+  rs.rot = uint32_t((rit >> 1) & 3);
   auto prefetch = [&](int64_t t, int b) {
     const int64_t row = t * kTile + rit;
-    const bool ok = t < n_tiles && row < p.n;
-    const float* src = p.rec + (ok ? row : 0) * kRecFloats;
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-      cp_async16(rec_row0 + uint32_t(b * 8192) + ((uint32_t(q) ^ rot) << 4), src + 4 * q, ok ? 16u : 0u);
-    cp_async_commit();
+    rs.fetch(p.rec, row, t < n_tiles && row < p.n, b);
   };
   int64_t tile = int64_t(blockIdx.x) * kSlots + slot;
   int buf = 0;
@@ -107,71 +217,104 @@ __global__ void __launch_bounds__(kInferThreads, 1) k_infer_tc(const __grid_cons
     prefetch(tile + stride, buf ^ 1);
     cp_async_wait<1>();  // this tile's record has landed (only this thread reads it)
     float r[kRecFloats];
-    {
-      const uint8_t* rowp = recs + slot * 2 * 8192 + buf * 8192 + rit * 64;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float4 v = *reinterpret_cast<const float4*>(rowp + ((uint32_t(q) ^ rot) << 4));
-        r[4 * q] = v.x;
-        r[4 * q + 1] = v.y;
-        r[4 * q + 2] = v.z;
-        r[4 * q + 3] = v.w;
-      }
-    }
+    rs.read(buf, r);
     buf ^= 1;
-    uint32_t pk[16];
-    {
-      float f[kEncDims];
-      encode_record<MODE>(r, p.pad, f);
-#pragma unroll
-      for (int j = 0; j < 16; ++j) pk[j] = pack2<BF16, false>(f[2 * j], f[2 * j + 1]);
-      tmem_st16(t_act, pk);
-#pragma unroll
-      for (int j = 0; j < 16; ++j) pk[j] = pack2<BF16, false>(f[32 + 2 * j], f[33 + 2 * j]);
-      tmem_st16(t_act + 16, pk);
-      tmem_st_wait();
-    }
-    for (int l = 0; l < p.n_mats; ++l) {
-      fence_before();
-      named_sync(1 + slot, 128);
-      if (rit == 0) {
-        fence_after();
-        const uint32_t idesc = idesc_f16(128, p.img.rows[l], BF16);
-        const uint32_t b0 = sw_base + uint32_t(p.img.off[l]);
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-          mma_ts(tmem + acc_col, tmem + act_col + uint32_t(k * 8), sdesc_sw128(b0 + uint32_t(k * 32), 16, 1024),
-                 idesc, k > 0 ? 1u : 0u);
-        mma_commit(&bar_mma[slot]);
-      }
-      // one thread waits for the MMAs; the rest of the warpgroup sleeps at the barrier
-      if (rit == 0) mbar_wait(&bar_mma[slot], phase, p.err);
-      named_sync(1 + slot, 128);
-      phase ^= 1u;
-      fence_after();
-      if (l + 1 < p.n_mats) {
-        uint32_t v[64];
-        tmem_ld64(t_acc, v);
-#pragma unroll
-        for (int j = 0; j < 16; ++j) pk[j] = pack2<BF16, true>(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
-        tmem_st16(t_act, pk);
-#pragma unroll
-        for (int j = 0; j < 16; ++j) pk[j] = pack2<BF16, true>(__uint_as_float(v[32 + 2 * j]), __uint_as_float(v[33 + 2 * j]));
-        tmem_st16(t_act + 16, pk);
-        tmem_st_wait();
-      } else {
-        uint32_t v[4];
-        tmem_ld4(t_acc, v);
-        if (row < p.n) {
-          float* o = p.rgb + row * 3;
-          o[0] = __uint_as_float(v[0]);
-          o[1] = __uint_as_float(v[1]);
-          o[2] = __uint_as_float(v[2]);
-        }
-      }
-    }
+    encode_to_tmem<MODE, BF16>(r, p.pad, st.t_act);
+    tile_layers<BF16>(p.img, p.n_mats, st, sw_base, slot, rit, &bar_mma[slot], phase, p.err,
+                      row < p.n ? p.rgb + row * 3 : nullptr);
   }
   cp_async_wait<0>();
+  fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after();
+    tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+// Batched inference over several caches (one persistent launch): the work is
+// a list of units, each a run of up to `unit_tiles` 128-row tiles of one
+// cache; CTAs take units from a device counter.  A CTA reloads the weight
+// image only when its next unit belongs to another cache; within a unit the
+// slots take the tiles round-robin exactly as k_infer_tc does, so every row's
+// arithmetic is the same as in a single-cache launch.
+template <int MODE, bool BF16>
+__global__ void __launch_bounds__(kInferThreads, 1) k_infer_batched(const __grid_constant__ BatchInferParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ uint64_t bar_w;
+  __shared__ uint64_t bar_mma[kSlots];
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int unit_sh;
+  uint8_t* sw = align1024(smem_raw);
+  uint8_t* recs = sw + ((p.img_bytes + 1023) & ~1023);
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  const int slot = tid >> 7;
+  const int rit = tid & 127;
+  if (warp == 0) {
+    tmem_alloc(&tmem_base_sh, kTmemCols);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    mbar_init(&bar_w, 1);
+    for (int s = 0; s < kSlots; ++s) mbar_init(&bar_mma[s], 1);
+    fence_barrier_init();
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_base_sh;
+  const uint32_t lane_base = uint32_t((warp & 3) * 32) << 16;
+  SlotTmem st;
+  st.tmem = tmem;
+  st.acc_col = uint32_t(slot * kSlotCols);
+  st.act_col = st.acc_col + 64;
+  st.t_acc = tmem + lane_base + st.acc_col;
+  st.t_act = tmem + lane_base + st.act_col;
+  const uint32_t sw_base = smem_u32(sw);
+  RecStage rs;
+  rs.row0 = smem_u32(recs) + uint32_t(slot * 2 * 8192 + rit * 64);
+  rs.p = recs + slot * 2 * 8192 + rit * 64;
+  rs.rot = uint32_t((rit >> 1) & 3);
+  int cur = -1;
+  uint32_t wphase = 0, phase = 0;
+  while (true) {
+    __syncthreads();  // every slot is done with the previous unit (its MMAs completed)
+    if (tid == 0) unit_sh = int(atomicAdd(p.counter, 1u));
+    __syncthreads();
+    const int u = unit_sh;
+    if (u >= p.n_units) break;
+    const BatchUnit U = p.units[u];
+    const BatchCache C = p.caches[U.cache];
+    if (U.cache != cur) {
+      if (tid == 0) {
+        mbar_arrive_expect_tx(&bar_w, uint32_t(p.img_bytes));
+        bulk_g2s(sw, C.wimg, uint32_t(p.img_bytes), &bar_w);
+      }
+      mbar_wait(&bar_w, wphase, p.err);
+      wphase ^= 1u;
+      cur = U.cache;
+    }
+    int buf = 0;
+    int64_t tile = U.tile_begin + slot;
+    auto prefetch = [&](int64_t t, int b) {
+      const int64_t row = t * kTile + rit;
+      rs.fetch(C.rec, row, t < U.tile_end && row < C.n, b);
+    };
+    prefetch(tile, buf);
+    for (; tile < U.tile_end; tile += kSlots) {
+      const int64_t row = tile * kTile + rit;
+      prefetch(tile + kSlots, buf ^ 1);
+      cp_async_wait<1>();
+      float r[kRecFloats];
+      rs.read(buf, r);
+      buf ^= 1;
+      encode_to_tmem<MODE, BF16>(r, p.pad, st.t_act);
+      tile_layers<BF16>(p.img, p.n_mats, st, sw_base, slot, rit, &bar_mma[slot], phase, p.err,
+                        row < C.n ? C.rgb + row * 3 : nullptr);
+    }
+    cp_async_wait<0>();
+  }
   fence_before();
   __syncthreads();
   if (warp == 0) {
@@ -227,6 +370,41 @@ cudaError_t launch_infer_tc(Cache* c, const float* rec, int64_t n, float* rgb, c
   return cudaGetLastError();
 }
 
+cudaError_t launch_infer_batched(const Cache* proto, const BatchCache* caches, const BatchUnit* units, int n_units,
+                                 unsigned* counter, int grid, cudaStream_t st) {
+  BatchInferParams p;
+  p.caches = caches;
+  p.units = units;
+  p.n_units = n_units;
+  p.counter = counter;
+  p.img_bytes = proto->img.off[proto->net.n_mats];
+  p.n_mats = proto->net.n_mats;
+  p.img = proto->img;
+  p.pad = proto->cfg.pad_value;
+  p.err = proto->err;
+  const int smem = ((p.img_bytes + 1023) & ~1023) + kSlots * 2 * 8192 + 1024;
+  const bool bf16 = proto->cfg.dtype == NRC_BF16;
+  const int mode = proto->cfg.enc_mode;
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  static int attr_done[4] = {0, 0, 0, 0};
+#define NRC_LAUNCH(M, B)                                                        \
+  e = set_smem(k_infer_batched<M, B>, smem, &attr_done[2 * (M) + ((B) ? 1 : 0)]); \
+  if (e != cudaSuccess) return e;                                               \
+  k_infer_batched<M, B><<<unsigned(grid), kInferThreads, smem, st>>>(p);
+  if (mode == 0 && !bf16) {
+    NRC_LAUNCH(0, false)
+  } else if (mode == 0 && bf16) {
+    NRC_LAUNCH(0, true)
+  } else if (!bf16) {
+    NRC_LAUNCH(1, false)
+  } else {
+    NRC_LAUNCH(1, true)
+  }
+#undef NRC_LAUNCH
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------- training
 // Fused training step on the tensor cores (Sec. 4, training the fully fused
 // network; Eq. 5; the weight-gradient contraction the paper leaves to a
@@ -251,6 +429,7 @@ constexpr int kTrainThreads = 256;
 constexpr int kTrainMaxMats = 6;  // TMEM: acc 64 + act 32 + 6 x 64 dW columns <= 512
 
 struct TrainParams {
+  const TrainJob* jobs;  // per-CTA work of a batched step over several caches; null: one cache (fields below)
   const float* pool;
   const float* target;
   int64_t n_pool;
@@ -348,8 +527,28 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(const __grid_cons
   const int L = p.n_mats;
   uint32_t phase = 0;
   float loss_acc = 0.0f;
-  const int64_t n_tiles = (p.batch + kTile - 1) / kTile;
   bool first = true;
+  // this CTA's work: tiles tile_begin, tile_begin + tile_step, ... < tile_end of one cache
+  TrainJob J;
+  if (p.jobs) {
+    J = p.jobs[blockIdx.x];
+  } else {
+    J.pool = p.pool;
+    J.target = p.target;
+    J.n_pool = p.n_pool;
+    J.batch = p.batch;
+    J.a = p.a;
+    J.c = p.c;
+    J.step = p.step;
+    J.tile_begin = int(blockIdx.x);
+    J.tile_end = int((p.batch + kTile - 1) / kTile);
+    J.tile_step = int(gridDim.x);
+    J.wimg = p.wimg;
+    J.partial = p.partials + size_t(blockIdx.x) * partial_stride(p.n_params);
+    J.t_ctr = p.t_ctr;
+    J.bump_t = blockIdx.x == 0;
+    J.inv3n = p.inv3n;
+  }
 
   // One dependent step: make this warpgroup pair's shared-memory and TMEM
   // writes visible, issue the MMAs (one thread), run `overlap` while they
@@ -376,7 +575,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(const __grid_cons
   // 16-byte chunk c of each 128-byte half at chunk c ^ (o % 8): conflict-free),
   // and after the next barrier all 256 threads copy it to the CTA's partial
   // with coalesced stores.
-  float* P = p.partials + size_t(blockIdx.x) * partial_stride(p.n_params);
+  float* P = J.partial;
   auto stage_dw = [&](int l) {
     if ((warp & 3) >= 2) return;
     const int o = r;
@@ -402,18 +601,18 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(const __grid_cons
     }
   };
 
-  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+  for (int64_t tile = J.tile_begin; tile < J.tile_end; tile += J.tile_step) {
     const int64_t j = tile * kTile + r;
-    const bool valid = j < p.batch;
+    const bool valid = j < J.batch;
     float rec[kRecFloats], tg[3] = {0.f, 0.f, 0.f};
     if (valid) {
-      const uint64_t i = uint64_t(p.step) * uint64_t(p.batch) + uint64_t(j);
-      const int64_t src = int64_t((p.a * i + p.c) % uint64_t(p.n_pool));
-      load_record(p.pool, src, rec);
+      const uint64_t i = uint64_t(J.step) * uint64_t(J.batch) + uint64_t(j);
+      const int64_t src = int64_t((J.a * i + J.c) % uint64_t(J.n_pool));
+      load_record(J.pool, src, rec);
       if (half == 0) {
-        tg[0] = __ldg(p.target + src * 3);
-        tg[1] = __ldg(p.target + src * 3 + 1);
-        tg[2] = __ldg(p.target + src * 3 + 2);
+        tg[0] = __ldg(J.target + src * 3);
+        tg[1] = __ldg(J.target + src * 3 + 1);
+        tg[2] = __ldg(J.target + src * 3 + 2);
       }
     } else {
 #pragma unroll
@@ -435,9 +634,9 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(const __grid_cons
       // partials belong to that step and are touched only after it completes.
       pdl_wait();
       if (tid == 0) {
-        if (blockIdx.x == 0) *p.t_ctr += 1;  // Adam's step counter for the update that follows
+        if (J.bump_t) *J.t_ctr += 1;  // Adam's step counter for the update that follows
         mbar_arrive_expect_tx(&bar_w, uint32_t(p.img_bytes));
-        bulk_g2s(sw, p.wimg, uint32_t(p.img_bytes), &bar_w);
+        bulk_g2s(sw, J.wimg, uint32_t(p.img_bytes), &bar_w);
       }
       mbar_wait(&bar_w, 0, p.err);
       have_w = true;
@@ -495,7 +694,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(const __grid_cons
     tmem_st_wait();
 
     // ----------------------------------------------------------- backward
-    const bool last_tile = tile + int64_t(gridDim.x) >= n_tiles;
+    const bool last_tile = tile + J.tile_step >= J.tile_end;
     for (int l = L - 1; l >= 0; --l) {
       const bool first_acc = first;
       mma_stage([&]() {
@@ -553,7 +752,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(const __grid_cons
   if (half == 0 && (tid & 31) == 0) red[warp] = s;
   fence_before();
   __syncthreads();
-  if (tid == 0) P[p.n_params] = ((red[0] + red[1]) + (red[2] + red[3])) * p.inv3n;
+  if (tid == 0) P[p.n_params] = ((red[0] + red[1]) + (red[2] + red[3])) * J.inv3n;
   if (warp == 0) {
     fence_after();
     tmem_dealloc(tmem, kTmemCols);
@@ -564,6 +763,7 @@ cudaError_t launch_train_tc(Cache* c, const float* pool, const float* target, in
                             uint64_t a, uint64_t cc, int step, int* n_partials, float* grad_scale, cudaStream_t st) {
   if (c->net.n_mats > kTrainMaxMats) return cudaErrorNotSupported;
   TrainParams p;
+  p.jobs = nullptr;
   p.pool = pool;
   p.target = target;
   p.n_pool = n_pool;
@@ -619,6 +819,56 @@ cudaError_t launch_train_tc(Cache* c, const float* pool, const float* target, in
 #undef NRC_LAUNCH
   *n_partials = grid;
   *grad_scale = p.inv3n;
+  return cudaGetLastError();
+}
+
+// One launch of the training kernel over several caches: CTA b runs jobs[b]
+// (device array); proto supplies the shape, dtype, encoding and loss
+// settings shared by the caches.
+cudaError_t launch_train_batched(const Cache* proto, const TrainJob* jobs, int n_jobs, cudaStream_t st) {
+  if (proto->net.n_mats > kTrainMaxMats) return cudaErrorNotSupported;
+  TrainParams p;
+  memset(&p, 0, sizeof(p));
+  p.jobs = jobs;
+  p.n_mats = proto->net.n_mats;
+  p.img = proto->img;
+  p.img_bytes = proto->img.off[proto->net.n_mats];
+  for (int l = 0; l <= kMaxMats; ++l) p.w_off[l] = proto->net.w_off[l];
+  p.n_params = proto->net.n_params;
+  p.pad = proto->cfg.pad_value;
+  p.loss_mode = proto->cfg.loss_mode;
+  p.loss_eps = proto->cfg.loss_eps;
+  p.err = proto->err;
+  const int smem = ((p.img_bytes + 1023) & ~1023) + p.n_mats * 16384 + 16384 + 1024;
+  const bool bf16 = proto->cfg.dtype == NRC_BF16;
+  const int mode = proto->cfg.enc_mode;
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3(unsigned(n_jobs));
+  lc.blockDim = dim3(kTrainThreads);
+  lc.dynamicSmemBytes = size_t(smem);
+  lc.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  lc.attrs = attr;
+  lc.numAttrs = 1;
+  cudaError_t e = cudaSuccess;
+  static int attr_done[4] = {0, 0, 0, 0};
+#define NRC_LAUNCH(M, B)                                                   \
+  e = set_smem(k_train_tc<M, B>, smem, &attr_done[2 * (M) + ((B) ? 1 : 0)]); \
+  if (e != cudaSuccess) return e;                                          \
+  e = cudaLaunchKernelEx(&lc, k_train_tc<M, B>, p);                        \
+  if (e != cudaSuccess) return e;
+  if (mode == 0 && !bf16) {
+    NRC_LAUNCH(0, false)
+  } else if (mode == 0 && bf16) {
+    NRC_LAUNCH(0, true)
+  } else if (!bf16) {
+    NRC_LAUNCH(1, false)
+  } else {
+    NRC_LAUNCH(1, true)
+  }
+#undef NRC_LAUNCH
   return cudaGetLastError();
 }
 

@@ -145,7 +145,6 @@ static nrc_status check_pool(const nrc_cache* c, const float* pool, const float*
 
 }  // namespace nrc
 
-struct nrc_cache : nrc::Cache {};
 
 using namespace nrc;
 

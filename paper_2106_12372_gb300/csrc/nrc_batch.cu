@@ -1,0 +1,285 @@
+// Batched caches: many independent caches (each its own weights, Adam state
+// and target field) queried in one persistent launch and trained in one
+// gradient launch plus one Adam launch per step, with a work-unit size chosen
+// by measurement (nrc_batch_autotune).
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "nrc_internal.cuh"
+
+namespace nrc {
+
+constexpr int kRing = 8;  // pinned descriptor slots in flight
+
+struct Batch {
+  std::vector<nrc_cache*> caches;
+  int unit_tiles = 20;
+  int max_units = 0;
+  int max_jobs = 0;
+  // device
+  BatchCache* d_caches = nullptr;
+  BatchUnit* d_units = nullptr;
+  unsigned* d_counter = nullptr;
+  TrainJob* d_jobs = nullptr;
+  AdamJob* d_adam = nullptr;
+  float* d_partials = nullptr;
+  // host: last uploaded query descriptors, pinned staging ring
+  std::vector<BatchCache> h_caches;
+  std::vector<BatchUnit> h_units;
+  uint8_t* pinned = nullptr;
+  size_t slot_bytes = 0;
+  cudaEvent_t ev[kRing] = {};
+  int ring = 0;
+  int sm_count = 0;
+};
+
+static size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// A pinned slot that no copy in flight still reads.
+static uint8_t* ring_slot(Batch* b, int* idx) {
+  const int i = b->ring;
+  b->ring = (b->ring + 1) % kRing;
+  cudaEventSynchronize(b->ev[i]);
+  *idx = i;
+  return b->pinned + size_t(i) * b->slot_bytes;
+}
+
+static bool same_cfg(const nrc_config& a, const nrc_config& b) {
+  return a.width == b.width && a.hidden_layers == b.hidden_layers && a.dtype == b.dtype && a.enc_mode == b.enc_mode &&
+         a.loss_mode == b.loss_mode && a.pad_value == b.pad_value && a.lr == b.lr && a.beta1 == b.beta1 &&
+         a.beta2 == b.beta2 && a.adam_eps == b.adam_eps && a.loss_eps == b.loss_eps;
+}
+
+}  // namespace nrc
+
+struct nrc_batch : nrc::Batch {};
+
+using namespace nrc;
+
+static void free_batch(nrc_batch* b) {
+  cudaFree(b->d_caches);
+  cudaFree(b->d_units);
+  cudaFree(b->d_counter);
+  cudaFree(b->d_jobs);
+  cudaFree(b->d_adam);
+  cudaFree(b->d_partials);
+  cudaFreeHost(b->pinned);
+  for (int i = 0; i < kRing; ++i)
+    if (b->ev[i]) cudaEventDestroy(b->ev[i]);
+  delete b;
+}
+
+extern "C" {
+
+nrc_status nrc_batch_create(nrc_cache* const* caches, int32_t n_caches, nrc_batch** out) {
+  if (!out || !caches || n_caches <= 0) return set_error("nrc_batch_create: no caches"), NRC_ERR_INVALID_ARG;
+  *out = nullptr;
+  for (int c = 0; c < n_caches; ++c) {
+    if (!caches[c]) return set_error("nrc_batch_create: cache %d is NULL", c), NRC_ERR_INVALID_ARG;
+    if (caches[c]->cfg.dtype == NRC_FP32)
+      return set_error("nrc_batch_create: batched caches compute in FP16 or BF16"), NRC_ERR_UNSUPPORTED;
+    if (!same_cfg(caches[c]->cfg, caches[0]->cfg))
+      return set_error("nrc_batch_create: cache %d differs in configuration from cache 0", c), NRC_ERR_INVALID_ARG;
+    if (caches[c]->device != caches[0]->device)
+      return set_error("nrc_batch_create: caches live on different devices"), NRC_ERR_INVALID_ARG;
+  }
+  nrc_batch* b = new (std::nothrow) nrc_batch();
+  if (!b) return set_error("host allocation failed"), NRC_ERR_OOM;
+  b->caches.assign(caches, caches + n_caches);
+  b->sm_count = caches[0]->sm_count;
+  b->max_jobs = b->sm_count;
+  b->max_units = 1 << 16;
+  const size_t stride = partial_stride(caches[0]->net.n_params);
+  b->slot_bytes = up256(sizeof(BatchCache) * n_caches) + up256(sizeof(BatchUnit) * b->max_units) +
+                  up256(sizeof(TrainJob) * b->max_jobs) + up256(sizeof(AdamJob) * n_caches);
+  cudaError_t e = cudaMalloc(&b->d_caches, sizeof(BatchCache) * n_caches);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_units, sizeof(BatchUnit) * b->max_units);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_jobs, sizeof(TrainJob) * b->max_jobs);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_adam, sizeof(AdamJob) * n_caches);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_partials, size_t(b->max_jobs) * stride * 4);
+  if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&b->pinned), b->slot_bytes * kRing, cudaHostAllocDefault);
+  for (int i = 0; i < kRing && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&b->ev[i], cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    nrc_status s = cuda_status(e, "nrc_batch_create");
+    free_batch(b);
+    return s;
+  }
+  *out = b;
+  return NRC_OK;
+}
+
+nrc_status nrc_batch_destroy(nrc_batch* b) {
+  if (!b) return NRC_OK;
+  cudaError_t e = cudaDeviceSynchronize();
+  free_batch(b);
+  return cuda_status(e, "nrc_batch_destroy");
+}
+
+nrc_status nrc_batch_set_unit_tiles(nrc_batch* b, int32_t unit_tiles) {
+  if (!b || unit_tiles < 1 || unit_tiles > 4096) return set_error("unit_tiles must be in [1, 4096]"), NRC_ERR_INVALID_ARG;
+  b->unit_tiles = unit_tiles;
+  return NRC_OK;
+}
+
+nrc_status nrc_batch_infer(nrc_batch* b, const float* const* records, const int64_t* n, float* const* rgb,
+                           nrc_stream stream) {
+  if (!b || !records || !n || !rgb) return set_error("nrc_batch_infer: NULL argument"), NRC_ERR_INVALID_ARG;
+  const int nc = int(b->caches.size());
+  std::vector<BatchCache> hc(static_cast<size_t>(nc));
+  std::vector<BatchUnit> hu;
+  for (int c = 0; c < nc; ++c) {
+    if (n[c] < 0) return set_error("nrc_batch_infer: n[%d] < 0", c), NRC_ERR_INVALID_ARG;
+    if (n[c] > 0 && (!records[c] || !rgb[c] || (reinterpret_cast<uintptr_t>(records[c]) & 15u)))
+      return set_error("nrc_batch_infer: buffers of cache %d NULL or misaligned", c), NRC_ERR_INVALID_ARG;
+    if (n[c] > (int64_t(1) << 38)) return set_error("nrc_batch_infer: n[%d] too large", c), NRC_ERR_INVALID_ARG;
+    hc[c] = BatchCache{b->caches[c]->wimg, records[c], rgb[c], n[c]};
+    const int64_t tiles = (n[c] + kTile - 1) / kTile;
+    for (int64_t t = 0; t < tiles; t += b->unit_tiles)
+      hu.push_back(BatchUnit{c, int(t), int(std::min<int64_t>(tiles, t + b->unit_tiles))});
+  }
+  if (hu.empty()) return NRC_OK;
+  if (int(hu.size()) > b->max_units) return set_error("nrc_batch_infer: too many work units"), NRC_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSuccess;
+  const bool same = hc.size() == b->h_caches.size() && hu.size() == b->h_units.size() &&
+                    !std::memcmp(hc.data(), b->h_caches.data(), sizeof(BatchCache) * hc.size()) &&
+                    !std::memcmp(hu.data(), b->h_units.data(), sizeof(BatchUnit) * hu.size());
+  if (!same) {  // descriptors are uploaded only when they change (a replayed graph reuses them)
+    int slot;
+    uint8_t* h = ring_slot(b, &slot);
+    std::memcpy(h, hc.data(), sizeof(BatchCache) * nc);
+    uint8_t* hu_p = h + up256(sizeof(BatchCache) * nc);
+    std::memcpy(hu_p, hu.data(), sizeof(BatchUnit) * hu.size());
+    e = cudaMemcpyAsync(b->d_caches, h, sizeof(BatchCache) * nc, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_units, hu_p, sizeof(BatchUnit) * hu.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev[slot], st);
+    if (e != cudaSuccess) return cuda_status(e, "nrc_batch_infer upload");
+    b->h_caches = hc;
+    b->h_units = hu;
+  }
+  const int grid = std::min<int>(b->sm_count, int(hu.size()));
+  e = launch_infer_batched(b->caches[0], b->d_caches, b->d_units, int(hu.size()), b->d_counter, grid, st);
+  for (auto* c : b->caches) c->launches += 1;
+  return cuda_status(e, "nrc_batch_infer");
+}
+
+nrc_status nrc_batch_train_step(nrc_batch* b, const float* const* pool, const float* const* target,
+                                const int64_t* n_pool, const int64_t* batch, const uint64_t* frame_seed,
+                                int32_t step, float* const* loss_out, nrc_stream stream) {
+  if (!b || !pool || !target || !n_pool || !batch || !frame_seed || step < 0)
+    return set_error("nrc_batch_train_step: NULL argument or negative step"), NRC_ERR_INVALID_ARG;
+  const int nc = int(b->caches.size());
+  const size_t stride = partial_stride(b->caches[0]->net.n_params);
+  std::vector<int64_t> tiles(size_t(nc), 0);
+  int64_t total = 0;
+  for (int c = 0; c < nc; ++c) {
+    if (batch[c] < 0 || batch[c] > kMaxBatch) return set_error("nrc_batch_train_step: batch[%d] out of range", c), NRC_ERR_INVALID_ARG;
+    if (batch[c] == 0) continue;
+    if (n_pool[c] >= (int64_t(1) << 31) || (int64_t(step) + 1) * batch[c] > n_pool[c])
+      return set_error("nrc_batch_train_step: (step+1)*batch[%d] exceeds n_pool or n_pool too large", c), NRC_ERR_INVALID_ARG;
+    if (!pool[c] || !target[c] || (reinterpret_cast<uintptr_t>(pool[c]) & 15u))
+      return set_error("nrc_batch_train_step: buffers of cache %d NULL or misaligned", c), NRC_ERR_INVALID_ARG;
+    tiles[c] = (batch[c] + kTile - 1) / kTile;
+    total += tiles[c];
+  }
+  if (total == 0) return NRC_OK;
+  // CTAs per cache in proportion to its tiles (at least one each), at most one per SM in all
+  const int budget = std::max(nc, b->max_jobs);
+  std::vector<int> k(size_t(nc), 0);
+  int used = 0;
+  for (int c = 0; c < nc; ++c)
+    if (tiles[c]) {
+      k[c] = int(std::max<int64_t>(1, std::min<int64_t>(tiles[c], budget * tiles[c] / total)));
+      used += k[c];
+    }
+  while (used > b->max_jobs) {  // trim the largest shares
+    int cmax = int(std::max_element(k.begin(), k.end()) - k.begin());
+    if (k[cmax] <= 1) return set_error("nrc_batch_train_step: more caches than CTAs"), NRC_ERR_UNSUPPORTED;
+    --k[cmax];
+    --used;
+  }
+  int slot;
+  uint8_t* h = ring_slot(b, &slot);
+  TrainJob* hj = reinterpret_cast<TrainJob*>(h);
+  AdamJob* ha = reinterpret_cast<AdamJob*>(h + up256(sizeof(TrainJob) * b->max_jobs));
+  int j = 0, n_adam = 0;
+  for (int c = 0; c < nc; ++c) {
+    if (!tiles[c]) continue;
+    nrc_cache* cc = b->caches[c];
+    uint64_t a, ic;
+    lcg_params(n_pool[c], frame_seed[c], &a, &ic);
+    const int j0 = j;
+    for (int q = 0; q < k[c]; ++q, ++j) {
+      TrainJob& J = hj[j];
+      J.pool = pool[c];
+      J.target = target[c];
+      J.n_pool = n_pool[c];
+      J.batch = batch[c];
+      J.a = a;
+      J.c = ic;
+      J.step = step;
+      J.tile_begin = int(tiles[c] * q / k[c]);
+      J.tile_end = int(tiles[c] * (q + 1) / k[c]);
+      J.tile_step = 1;
+      J.wimg = cc->wimg;
+      J.partial = b->d_partials + size_t(j) * stride;
+      J.t_ctr = cc->t;
+      J.bump_t = q == 0;
+      J.inv3n = float(1.0 / (3.0 * double(batch[c])));
+    }
+    ha[n_adam++] = AdamJob{cc->w, cc->m, cc->v, cc->t, b->d_partials + size_t(j0) * stride, k[c], cc->wimg,
+                           float(1.0 / (3.0 * double(batch[c]))), loss_out ? loss_out[c] : nullptr};
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(b->d_jobs, hj, sizeof(TrainJob) * j, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_adam, ha, sizeof(AdamJob) * n_adam, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaEventRecord(b->ev[slot], st);
+  if (e == cudaSuccess) e = launch_train_batched(b->caches[0], b->d_jobs, j, st);
+  if (e == cudaSuccess) e = launch_adam_batched(b->caches[0], b->d_adam, n_adam, st);
+  for (auto* c : b->caches) c->launches += 2;
+  return cuda_status(e, "nrc_batch_train_step");
+}
+
+nrc_status nrc_batch_autotune(nrc_batch* b, const float* const* records, const int64_t* n, float* const* rgb,
+                              nrc_stream stream, int32_t* chosen) {
+  if (!b) return set_error("batch is NULL"), NRC_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int cand[] = {5, 10, 20, 40, 80, 160};
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int best_u = b->unit_tiles;
+  for (int u : cand) {
+    b->unit_tiles = u;
+    float t_min = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+      cudaEventRecord(e0, st);
+      nrc_status s = nrc_batch_infer(b, records, n, rgb, stream);
+      if (s != NRC_OK) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return s;
+      }
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) t_min = std::min(t_min, ms);  // the first run of each size includes the descriptor upload
+    }
+    if (t_min < best) {
+      best = t_min;
+      best_u = u;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->unit_tiles = best_u;
+  if (chosen) *chosen = best_u;
+  return cuda_status(cudaGetLastError(), "nrc_batch_autotune");
+}
+
+}  // extern "C"

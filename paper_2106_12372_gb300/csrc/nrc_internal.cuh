@@ -71,6 +71,50 @@ struct Cache {
   int device = 0;
 };
 
+// One cache of a batched query: its weight image and its query buffers.
+struct BatchCache {
+  const uint8_t* wimg;
+  const float* rec;
+  float* rgb;
+  int64_t n;
+};
+// A run of 128-row tiles [tile_begin, tile_end) of one cache.
+struct BatchUnit {
+  int cache;
+  int tile_begin;
+  int tile_end;
+};
+
+// The work of one CTA of a batched training step: tiles tile_begin,
+// tile_begin + tile_step, ... < tile_end of one cache's batch.
+struct TrainJob {
+  const float* pool;
+  const float* target;
+  int64_t n_pool;
+  int64_t batch;
+  uint64_t a, c;       // the batch's shuffle (Sec. 3.5)
+  int step;
+  int tile_begin, tile_end, tile_step;
+  const uint8_t* wimg;
+  float* partial;      // this CTA's weight-gradient partial
+  long long* t_ctr;
+  int bump_t;          // the cache's first CTA advances its Adam step counter
+  float inv3n;
+};
+
+// Adam over one cache of a batched step: its state and its partials.
+struct AdamJob {
+  float* w;
+  float* m;
+  float* v;
+  const long long* t_ctr;
+  const float* partials;
+  int n_partials;
+  uint8_t* wimg;
+  float grad_scale;
+  float* loss_out;
+};
+
 // ---------------------------------------------------------------- host side
 void set_error(const char* fmt, ...);
 nrc_status cuda_status(cudaError_t e, const char* what);
@@ -96,8 +140,16 @@ cudaError_t launch_adam(Cache* c, int n_partials, float grad_scale, float* loss_
 cudaError_t launch_build_image(Cache* c, cudaStream_t st);
 cudaError_t launch_step_increment(Cache* c, cudaStream_t st);
 cudaError_t launch_infer_tc(Cache* c, const float* rec, int64_t n, float* rgb, cudaStream_t st);
+// One persistent launch over the units of several caches (device arrays);
+// proto supplies the shape, dtype and encoding shared by all of them.
+cudaError_t launch_infer_batched(const Cache* proto, const BatchCache* caches, const BatchUnit* units, int n_units,
+                                 unsigned* counter, int grid, cudaStream_t st);
 cudaError_t launch_train_tc(Cache* c, const float* pool, const float* target, int64_t n_pool, int64_t batch,
                             uint64_t a, uint64_t cc, int step, int* n_partials, float* grad_scale, cudaStream_t st);
+// One training launch over several caches (device array of per-CTA jobs) and
+// one Adam launch over their weights.
+cudaError_t launch_train_batched(const Cache* proto, const TrainJob* jobs, int n_jobs, cudaStream_t st);
+cudaError_t launch_adam_batched(const Cache* proto, const AdamJob* jobs, int n_jobs, cudaStream_t st);
 // Plain per-layer FP32 path.
 cudaError_t plain_infer(Cache* c, const float* rec, int64_t n, float* rgb, cudaStream_t st);
 cudaError_t plain_train(Cache* c, const float* pool, const float* target, int64_t n_pool, int64_t batch,
@@ -229,3 +281,6 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 }
 
 }  // namespace nrc
+
+// The C ABI's opaque cache handle is the library's cache state.
+struct nrc_cache : nrc::Cache {};

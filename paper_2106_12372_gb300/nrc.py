@@ -87,6 +87,12 @@ def lib() -> ctypes.CDLL:
             "nrc_launch_count": (i64, [P]),
             "nrc_last_error_string": (ctypes.c_char_p, []),
             "nrc_train_step_noalloc": (i32, [P, P, P, P, P, P, P, i64, i64, u64, i32, P, P, P]),
+            "nrc_batch_create": (i32, [P, i32, P]),
+            "nrc_batch_destroy": (i32, [P]),
+            "nrc_batch_infer": (i32, [P, P, P, P, P]),
+            "nrc_batch_train_step": (i32, [P, P, P, P, P, P, i32, P, P]),
+            "nrc_batch_set_unit_tiles": (i32, [P, i32]),
+            "nrc_batch_autotune": (i32, [P, P, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -235,3 +241,55 @@ class Cache:
 
     def check_error(self, stream=None) -> None:
         _check(lib().nrc_check_error(self._h, _stream(stream)))
+
+
+def _ptr_array(tensors):
+    arr = (ctypes.c_void_p * len(tensors))()
+    for i, t in enumerate(tensors):
+        arr[i] = _ptr(t)
+    return arr
+
+
+class Batch:
+    """Several caches served together: one persistent query launch, one training launch per step."""
+
+    def __init__(self, caches):
+        self.caches = list(caches)
+        handles = (ctypes.c_void_p * len(self.caches))(*[c.handle for c in self.caches])
+        h = ctypes.c_void_p()
+        _check(lib().nrc_batch_create(handles, len(self.caches), ctypes.byref(h)))
+        self._h = h
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().nrc_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def infer(self, records, rgb, stream=None) -> None:
+        n = (ctypes.c_int64 * len(records))(*[r.shape[0] for r in records])
+        _check(lib().nrc_batch_infer(self._h, _ptr_array(records), n, _ptr_array(rgb), _stream(stream)))
+
+    def train_step(self, pools, targets, batches, frame_seeds, step: int, losses=None, stream=None) -> None:
+        k = len(pools)
+        n_pool = (ctypes.c_int64 * k)(*[p.shape[0] for p in pools])
+        bs = (ctypes.c_int64 * k)(*batches)
+        fs = (ctypes.c_uint64 * k)(*[s & (2**64 - 1) for s in frame_seeds])
+        lo = _ptr_array(losses) if losses is not None else None
+        _check(lib().nrc_batch_train_step(self._h, _ptr_array(pools), _ptr_array(targets), n_pool, bs, fs, step, lo,
+                                          _stream(stream)))
+
+    def set_unit_tiles(self, u: int) -> None:
+        _check(lib().nrc_batch_set_unit_tiles(self._h, u))
+
+    def autotune(self, records, rgb, stream=None) -> int:
+        n = (ctypes.c_int64 * len(records))(*[r.shape[0] for r in records])
+        chosen = ctypes.c_int32()
+        _check(lib().nrc_batch_autotune(self._h, _ptr_array(records), n, _ptr_array(rgb), _stream(stream),
+                                        ctypes.byref(chosen)))
+        return chosen.value

@@ -1,0 +1,143 @@
+"""Batched caches (several independent caches served together) on the GPU.
+
+* one persistent query launch over caches with uneven query counts gives, row
+  for row, exactly the single-cache result (same arithmetic per row);
+* one batched training step matches the FP64 oracle per cache, within the
+  16-bit path's tolerance;
+* the autotuner picks a candidate work-unit size and the results do not
+  depend on it; the batched query replays from a captured CUDA graph.
+"""
+import numpy as np
+import pytest
+
+from paper_2106_12372_gb300 import synth
+from parity import rel_err, stats
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU containers
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+from oracle import oracle as O  # noqa: E402
+from paper_2106_12372_gb300 import build, nrc  # noqa: E402
+
+DEV = torch.device("cuda:0")
+DIMS = synth.layer_dims()
+NS = [1, 127, 129, 1000, 0, 40_000, 262_144, 5_003]
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+@pytest.fixture(scope="module")
+def setup():
+    build.build()
+    caches, recs, ws = [], [], []
+    for k, n in enumerate(NS):
+        c = nrc.Cache(dtype="fp16", seed=500 + k)
+        w = synth.xavier_weights(DIMS, seed=500 + k)
+        c.set_state(w)
+        caches.append(c)
+        ws.append(w)
+        recs.append(dev(synth.make_records(max(n, 0), seed=600 + k)))
+    return caches, recs, ws
+
+
+def _single(caches, recs):
+    return [c.infer(r) if r.shape[0] else torch.empty((0, 3), device=DEV) for c, r in zip(caches, recs)]
+
+
+@pytest.mark.parametrize("unit", [1, 7, 20, 160])
+def test_batch_infer_equals_single_cache(setup, unit):
+    caches, recs, _ = setup
+    ref = _single(caches, recs)
+    b = nrc.Batch(caches)
+    b.set_unit_tiles(unit)
+    out = [torch.full((r.shape[0], 3), float("nan"), device=DEV) for r in recs]
+    b.infer(recs, out)
+    torch.cuda.synchronize()
+    for k in range(len(NS)):
+        assert torch.equal(out[k], ref[k]), (unit, k)
+    for c in caches:
+        c.check_error()
+
+
+def test_batch_infer_matches_oracle(setup):
+    caches, recs, ws = setup
+    b = nrc.Batch(caches)
+    out = [torch.empty((r.shape[0], 3), device=DEV) for r in recs]
+    b.infer(recs, out)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(0)
+    for k, n in enumerate(NS):
+        if n == 0:
+            continue
+        idx = rng.choice(n, min(n, 500), replace=False)
+        ref = O.infer(ws[k], DIMS, recs[k].cpu().numpy()[idx])
+        assert rel_err(out[k].cpu().numpy()[idx], ref).max() <= 2e-2, k
+
+
+def test_batch_autotune_and_graph_replay(setup):
+    caches, recs, _ = setup
+    ref = _single(caches, recs)
+    b = nrc.Batch(caches)
+    out = [torch.empty((r.shape[0], 3), device=DEV) for r in recs]
+    chosen = b.autotune(recs, out)
+    assert chosen in (5, 10, 20, 40, 80, 160)
+    b.infer(recs, out)  # uploads the descriptors for this unit size before capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for o in out:
+            o.fill_(float("nan"))
+        with torch.cuda.graph(g, stream=s):
+            b.infer(recs, out, stream=s)
+    for o in out:
+        o.fill_(float("nan"))
+    g.replay()
+    torch.cuda.synchronize()
+    for k in range(len(NS)):
+        assert torch.equal(out[k], ref[k]), k
+
+
+def test_batch_train_step_matches_oracle():
+    build.build()
+    batches = [16384, 4096, 1000, 65536 // 4]
+    caches, states, pools, tgts, fss = [], [], [], [], []
+    for k, bs in enumerate(batches):
+        w = synth.xavier_weights(DIMS, seed=700 + k)
+        c = nrc.Cache(dtype="fp16", seed=700 + k)
+        c.set_state(w)
+        caches.append(c)
+        states.append(O.TrainState(w, DIMS))
+        p, t = synth.make_training_pool(bs * 4, seed=800 + k)
+        pools.append(p)
+        tgts.append(t)
+        fss.append(synth.frame_seed(900 + k, 0))
+    b = nrc.Batch(caches)
+    losses = [torch.zeros(1, device=DEV) for _ in caches]
+    b.train_step([dev(p) for p in pools], [dev(t) for t in tgts], batches, fss, 2, losses)
+    torch.cuda.synchronize()
+    for k, c in enumerate(caches):
+        ref_loss, ref_g = states[k].step(pools[k], tgts[k], batches[k], fss[k], 2, want_grad=True)
+        w, m, v, t = c.get_state()
+        g = m.astype(np.float64) / (1.0 - 0.9)
+        print("batched train", k, batches[k], stats(g, ref_g))
+        assert t == 1
+        assert abs(losses[k].item() - ref_loss) <= 2e-2 * abs(ref_loss)
+        assert np.linalg.norm(g - ref_g) <= 2e-2 * np.linalg.norm(ref_g)
+        c.check_error()
+
+
+def test_batch_rejects_mixed_configurations():
+    build.build()
+    a = nrc.Cache(dtype="fp16")
+    b16 = nrc.Cache(dtype="bf16")
+    with pytest.raises(nrc.NrcError):
+        nrc.Batch([a, b16])
+    f32 = nrc.Cache(dtype="fp32")
+    with pytest.raises(nrc.NrcError):
+        nrc.Batch([f32])
