@@ -149,6 +149,170 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(queries, dtype: str, frames: int, flush):
+    """16 independent caches in one persistent query launch (replayed from a
+    CUDA graph) and one batched training step per frame.  Per-frame query
+    counts are log-uniform in [4,096, 2,097,152] and training batches
+    log-uniform in [4,096, 65,536] (seed 2110); cache k has its own weights
+    and target field (seed 2106 + 100 k).  Query records are views into the
+    two 2,073,600-record sets of the frame benchmark."""
+    import numpy as np
+    import torch
+
+    from paper_2106_12372_gb300 import nrc, synth
+
+    dev = queries[0].device
+    rng = np.random.default_rng(2106 + 4)
+    nq = np.exp(rng.uniform(np.log(4096), np.log(2097152), 16)).round().astype(np.int64)
+    bt = np.exp(rng.uniform(np.log(4096), np.log(65536), 16)).round().astype(np.int64)
+    allq = torch.cat(queries)
+    recs, rgbs, pools, tgts, caches = [], [], [], [], []
+    for k in range(16):
+        off = (k * 262144) % (allq.shape[0] - int(nq[k]))
+        recs.append(allq[off: off + int(nq[k])])
+        rgbs.append(torch.empty((int(nq[k]), 3), device=dev))
+        p, t = synth.make_training_pool(int(bt[k]), seed=2106 + 100 * k)
+        pools.append(torch.from_numpy(p).to(dev))
+        tgts.append(torch.from_numpy(t).to(dev))
+        caches.append(nrc.Cache(dtype=dtype, seed=2106 + 100 * k))
+    losses = [torch.zeros(1, device=dev) for _ in range(16)]
+    s = torch.cuda.Stream()
+    b = nrc.Batch(caches)
+    with torch.cuda.stream(s):
+        unit = b.autotune(recs, rgbs, stream=s)
+        b.infer(recs, rgbs, stream=s)
+        s.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            b.infer(recs, rgbs, stream=s)
+        bl = [int(x) for x in bt]
+
+        def frame(f, ev=None):
+            if ev:
+                ev[0].record(s)
+            g.replay()
+            if ev:
+                ev[1].record(s)
+            b.train_step(pools, tgts, bl, [synth.frame_seed(2106 + 100 * k, f) for k in range(16)], 0, losses,
+                         stream=s)
+            if ev:
+                ev[2].record(s)
+
+        for f in range(3):
+            frame(f)
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(frames)]
+        for f in range(frames):
+            flush.zero_()
+            frame(3 + f, evs[f])
+        # the same work as 16 separate caches, one query and one training call each
+        sev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(5)]
+        for f in range(5):
+            flush.zero_()
+            sev[f][0].record(s)
+            for k in range(16):
+                caches[k].infer(recs[k], rgbs[k], stream=s)
+                caches[k].train_step(pools[k], tgts[k], bl[k], synth.frame_seed(2106 + 100 * k, 100 + f), 0,
+                                     loss_out=losses[k], stream=s)
+            sev[f][1].record(s)
+        s.synchronize()
+    for c in caches:
+        c.check_error()
+    ms = [e[0].elapsed_time(e[2]) for e in evs]
+    inf = [e[0].elapsed_time(e[1]) for e in evs]
+    seq = [e[0].elapsed_time(e[1]) for e in sev[1:]]
+    q = int(nq.sum())
+    flop = FLOP_QUERY * q + FLOP_RECORD * int(bt.sum())
+    med = statistics.median(ms)
+    b.close()
+    for c in caches:
+        c.close()
+    return {
+        "workload": "16 caches: queries log-uniform [4096, 2097152], one training step of log-uniform [4096, 65536] "
+                    "records each; query launch replayed from a CUDA graph; L2 flushed between frames",
+        "queries": q, "train_records": int(bt.sum()), "frames": frames,
+        "ms_median": med, "ms_p99": float(np.percentile(ms, 99)), "infer_ms_median": statistics.median(inf),
+        "mqueries_per_s": q / (med / 1e3) / 1e6, "tflops": flop / (med / 1e3) / 1e12,
+        "unit_tiles_autotuned": unit, "launches_per_frame": 3,
+        "sequential_16_caches_ms_median": statistics.median(seq),
+    }
+
+
+def run_serving(queries, dtype: str, seconds: float):
+    """Eight viewports (4 x 1920x1080, 4 x 3840x2160) with Poisson frame
+    arrivals at 30-120 Hz each (rates seeded), served by the continuous-
+    batching server under a 16 GB memory budget; each frame is a cache query
+    for every pixel plus 4 training steps of 16,384 records from the
+    viewport's resident 65,536-record pool.  Latency runs from the frame's
+    scheduled arrival to the host callback at the end of its batch."""
+    import numpy as np
+    import torch
+
+    from paper_2106_12372_gb300 import nrc, synth
+
+    srv = nrc.Server(nrc.default_config(dtype=dtype))
+    rng = np.random.default_rng(2106 + 5)
+    sizes = [1920 * 1080] * 4 + [3840 * 2160] * 4
+    vps = []
+    for v, n in enumerate(sizes):
+        vid = srv.open_viewport(n, N_POOL, n_slots=2, seed=2106 + 500 + v)
+        pool, tgt, _ = srv.pool(vid)
+        p, t = synth.make_training_pool(N_POOL, seed=2106 + 500 + v)
+        pool.copy_(torch.from_numpy(p))
+        tgt.copy_(torch.from_numpy(t))
+        for slot in range(2):
+            r, _, _ = srv.buffers(vid, slot)
+            for j in range(n // N_QUERIES):
+                r[j * N_QUERIES:(j + 1) * N_QUERIES].copy_(queries[(j + slot) % 2])
+        vps.append((vid, n, float(rng.uniform(30.0, 120.0))))
+    torch.cuda.synchronize()
+    info0 = srv.info()
+    # warm-up: two frames per viewport
+    for f in range(2):
+        for vid, n, _ in vps:
+            while not srv.submit(vid, f % 2, n, synth.frame_seed(vid, f)):
+                srv.poll(timeout_ms=5)
+    srv.drain()
+    srv.poll(max_out=4096)
+    arrivals = []
+    for vid, n, rate in vps:
+        t = rng.exponential(1.0 / rate)
+        while t < seconds:
+            arrivals.append((t, vid, n))
+            t += rng.exponential(1.0 / rate)
+    arrivals.sort()
+    nxt = {vid: 2 for vid, _, _ in vps}
+    done = []
+    t0 = nrc.now_ns() + 1_000_000
+    for t, vid, n in arrivals:
+        due = t0 + int(t * 1e9)
+        while nrc.now_ns() < due:
+            done += srv.poll(timeout_ms=0)
+            if due - nrc.now_ns() > 300_000:
+                time.sleep(0.0001)
+        f = nxt[vid]
+        while not srv.submit(vid, f % 2, n, synth.frame_seed(vid, f), arrival_ns=due, tag=f):
+            done += srv.poll(timeout_ms=1)
+        nxt[vid] += 1
+    srv.drain()
+    done += srv.poll(max_out=65536)
+    info = srv.info()
+    srv.close()
+    lat = np.array([(d.done_ns - d.arrival_ns) / 1e6 for d in done])
+    span = (max(d.done_ns for d in done) - t0) / 1e9
+    q = sum(d.n_queries for d in done)
+    offered = sum(rate * n for _, n, rate in vps)
+    return {
+        "workload": "8 viewports (4 x 1920x1080, 4 x 3840x2160), Poisson arrivals 30-120 Hz each, per frame all "
+                    "pixels queried + 4 x 16,384-record training steps; 16 GB admission budget",
+        "seconds": seconds, "frames": len(done), "failed": int(sum(d.failed for d in done)),
+        "p50_frame_ms": float(np.percentile(lat, 50)), "p99_frame_ms": float(np.percentile(lat, 99)),
+        "max_frame_ms": float(lat.max()), "mean_batch_frames": float(np.mean([d.batch_frames for d in done])),
+        "aggregate_mqueries_per_s": q / span / 1e6, "offered_mqueries_per_s": offered / 1e6,
+        "rates_hz": [round(r, 1) for _, _, r in vps], "resident_gb": info0.memory_used / 1e9,
+        "batches": int(info.batches),
+    }
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -234,6 +398,11 @@ def run_gpu(args):
             plain_ms.append(pev[0].elapsed_time(pev[1]))
     plain.close()
 
+    batched = serving = None
+    if not args.no_extras and ws == 1 and args.dtype != "fp32":
+        batched = run_batched(queries, args.dtype, 30, flush)
+        serving = run_serving(queries, args.dtype, args.serve_seconds)
+
     # end to end: host (pinned) buffers through nrc_frame_host, copies inside the timed region
     qh = torch.from_numpy(synth.make_records(N_QUERIES, seed=seed + 7)).pin_memory()
     ph, th = pool.cpu().pin_memory(), tgt.cpu().pin_memory()
@@ -273,6 +442,8 @@ def run_gpu(args):
         "train_ms_median": statistics.median(train_ms),
         "frame_tflops": frame_flop / (med / 1e3) / 1e12, "frame_frac_of_peak": frame_flop / (med / 1e3) / 1e12 / burst,
         "plain_fp32_ms_per_frame": statistics.median(plain_ms) if plain_ms else None,
+        "batched_caches": batched,
+        "serving": serving,
         "roofline": {"kernel": "k_infer_tc (fused encode + 6 tcgen05 layers)", "bound": "tensor", "achieved": achieved,
                      "peak": burst, "unit": "TFLOP/s", "frac": achieved / burst, "traffic": None,
                      "peak_source": f"{src} bf16 dense burst (fp16 peak = bf16 peak)"},
@@ -295,6 +466,8 @@ def main():
     ap.add_argument("--dtype", default="fp16", choices=["fp16", "bf16", "fp32"])
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched-caches and serving measurements")
+    ap.add_argument("--serve-seconds", type=float, default=3.0)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -64,7 +64,8 @@ typedef enum nrc_status {
   NRC_ERR_CUDA = 2,
   NRC_ERR_OOM = 3,
   NRC_ERR_TIMEOUT = 4,
-  NRC_ERR_UNSUPPORTED = 5
+  NRC_ERR_UNSUPPORTED = 5,
+  NRC_ERR_BUSY = 6 /* not admitted now (memory budget or frame slot in use): retry later */
 } nrc_status;
 
 /* Arithmetic type of the MLP's matrix products.  NRC_FP32: FP32 SIMT FMA
@@ -234,11 +235,132 @@ NRC_API nrc_status nrc_batch_train_step(nrc_batch* batch, const float* const* po
 /* Sets the work-unit size of nrc_batch_infer (1 .. 4096 tiles; default 20). */
 NRC_API nrc_status nrc_batch_set_unit_tiles(nrc_batch* batch, int32_t unit_tiles);
 
+/* Training partition of nrc_batch_train_step.  0 (default): the CTAs (one
+ * per SM in all) are shared out in proportion to the caches' batches.
+ * T > 0 (up to 4096): cache c gets ceil(tiles_c / T) CTAs, tiles_c = its
+ * batch in 128-record tiles, whatever the other caches train; its weight
+ * gradients are then summed in the same order as when it trains alone, so
+ * its result is bit-identical alone and in any mix. */
+NRC_API nrc_status nrc_batch_set_train_tiles(nrc_batch* batch, int32_t train_tiles);
+
 /* Autotuner: runs nrc_batch_infer on the given buffers with each candidate
  * work-unit size (5 .. 160 tiles), keeps the fastest (CUDA-event timing; it
  * synchronises the stream) and reports it in *chosen (may be NULL). */
 NRC_API nrc_status nrc_batch_autotune(nrc_batch* batch, const float* const* records, const int64_t* n,
                                       float* const* rgb, nrc_stream stream, int32_t* chosen);
+
+/* ----------------------------------------------------------------------
+ * Serving runtime: frames streamed from several viewports, each with its own
+ * cache, batched continuously onto this GPU (the paper renders one viewport;
+ * this is the multi-viewport serving form of its per-frame work, Sec. 3.4 and
+ * Fig. 4: per frame, cache queries for every pixel's path vertex, then the
+ * frame's training steps).
+ *
+ * A viewport keeps resident on the device, owned by the server: its cache
+ * (weights, Adam state), its training-record pool with targets, and n_slots
+ * frame buffers (query records in, RGB out, per-step losses).  It is admitted
+ * only if that memory fits the server's budget.  The caller writes a frame's
+ * query records into a slot's buffer, the training pool into the pool buffer
+ * (both with work complete before it submits), and submits the frame; a
+ * scheduler thread batches pending frames -- in arrival order, at most one
+ * per viewport -- into one persistent query launch followed by train_steps
+ * batched training steps (viewport v's frame trains on batch k of the
+ * frame seed's shuffle of its pool in step k, Sec. 3.5), keeping at most
+ * max_inflight batches queued on the server's stream.  Frames arriving while
+ * a batch runs join the next batch.  Every viewport trains with the same CTA
+ * partition alone and in any mix (train_tiles), so a frame's outputs and the
+ * viewport's weights are bit-identical whatever else is served.
+ */
+typedef struct nrc_server nrc_server;
+
+typedef struct nrc_server_config {
+  uint64_t memory_budget; /* bytes all viewports may keep resident (default 16 GiB) */
+  int32_t max_viewports;  /* viewports open at once (default 16) */
+  int32_t max_inflight;   /* batches queued on the GPU at once (default 2) */
+  int32_t train_steps;    /* training steps per frame (default 4) */
+  int32_t train_batch;    /* records per training step (default 16384, <= 65536) */
+  int32_t train_tiles;    /* 128-record tiles per training CTA (default 4) */
+  int32_t unit_tiles;     /* 128-row tiles per query work unit (default 20) */
+} nrc_server_config;
+
+/* One finished frame.  Times are CLOCK_MONOTONIC nanoseconds (nrc_now_ns). */
+typedef struct nrc_frame_done {
+  int32_t viewport;
+  int32_t slot;
+  int64_t tag;          /* the caller's tag from nrc_server_submit */
+  int64_t n_queries;
+  int64_t arrival_ns;   /* the caller's arrival time from nrc_server_submit */
+  int64_t submit_ns;    /* when nrc_server_submit accepted it */
+  int64_t launch_ns;    /* when its batch was issued */
+  int64_t done_ns;      /* when the stream reached the end of its batch */
+  int32_t batch_frames; /* frames in its batch */
+  int32_t failed;       /* 1 if its batch failed to launch (see nrc_server_poll's status) */
+} nrc_frame_done;
+
+typedef struct nrc_server_info {
+  uint64_t memory_used;
+  uint64_t memory_budget;
+  int64_t frames_done;
+  int64_t batches;
+  int64_t queries_done;
+  int64_t pending;
+  int32_t viewports;
+  int32_t inflight;
+} nrc_server_info;
+
+NRC_API void nrc_server_default_config(nrc_server_config* cfg);
+
+/* Monotonic clock of the frame timings, in nanoseconds. */
+NRC_API int64_t nrc_now_ns(void);
+
+/* Creates a server for caches of configuration *cache_cfg (NRC_FP16 or
+ * NRC_BF16; every viewport's cache must equal it but for the seed) on the
+ * current device, with its own non-blocking stream and scheduler thread. */
+NRC_API nrc_status nrc_server_create(const nrc_server_config* cfg, const nrc_config* cache_cfg, nrc_server** out);
+
+/* Waits for every submitted frame, stops the thread, frees all viewports. */
+NRC_API nrc_status nrc_server_destroy(nrc_server* server);
+
+/* Admits a viewport: creates its cache from *cache_cfg (Xavier init from
+ * cache_cfg->seed) and allocates its pool (n_pool >= train_steps x
+ * train_batch records) and n_slots (1..8) frame buffers of max_queries
+ * records.  NRC_ERR_BUSY if the memory would exceed the budget or all
+ * viewport entries are in use (nothing allocated; retry after a close).
+ * *id_out receives the viewport id. */
+NRC_API nrc_status nrc_server_open_viewport(nrc_server* server, const nrc_config* cache_cfg, int64_t max_queries,
+                                            int64_t n_pool, int32_t n_slots, int32_t* id_out);
+
+/* Waits for the viewport's frames, then frees its cache and buffers. */
+NRC_API nrc_status nrc_server_close_viewport(nrc_server* server, int32_t id);
+
+/* Device pointers of a slot's buffers (server-owned): records [max_queries][16]
+ * (caller writes), rgb [max_queries][3] and losses [train_steps] (valid once
+ * the frame is reported done).  Any out-pointer may be NULL. */
+NRC_API nrc_status nrc_server_viewport_buffers(nrc_server* server, int32_t id, int32_t slot, float** records,
+                                               float** rgb, float** losses);
+
+/* Device pointers of the viewport's training pool [n_pool][16] and targets
+ * [n_pool][3] (caller writes) and its cache handle (for nrc_get_state /
+ * nrc_set_state after nrc_server_drain; the server owns it). */
+NRC_API nrc_status nrc_server_viewport_pool(nrc_server* server, int32_t id, float** pool, float** target,
+                                            nrc_cache** cache);
+
+/* Queues frame `tag` of viewport `id`: n_queries (<= max_queries) records in
+ * slot `slot`, training shuffle seeded by frame_seed.  NRC_ERR_BUSY while the
+ * slot's previous frame is in flight.  Does not block. */
+NRC_API nrc_status nrc_server_submit(nrc_server* server, int32_t id, int32_t slot, int64_t n_queries,
+                                     uint64_t frame_seed, int64_t arrival_ns, int64_t tag);
+
+/* Moves up to max_out finished frames into out[] (*n_out of them), waiting up
+ * to timeout_ms for the first if none is ready.  Returns the first error a
+ * batch met, if any (its frames are reported with failed = 1). */
+NRC_API nrc_status nrc_server_poll(nrc_server* server, nrc_frame_done* out, int32_t max_out, int32_t timeout_ms,
+                                   int32_t* n_out);
+
+/* Blocks until every submitted frame is done and the stream is idle. */
+NRC_API nrc_status nrc_server_drain(nrc_server* server);
+
+NRC_API nrc_status nrc_server_query(nrc_server* server, nrc_server_info* out);
 
 /* Training step that allocates nothing (the paper has no counterpart; this
  * serves callers that cannot allocate device memory when they train -- e.g.

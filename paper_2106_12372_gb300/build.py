@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnrc.so")
-SOURCES = ["nrc_api.cu", "k_simt.cu", "k_tc.cu", "k_plain.cu", "nrc_noalloc.cu", "nrc_batch.cu"]
+SOURCES = ["nrc_api.cu", "k_simt.cu", "k_tc.cu", "k_plain.cu", "nrc_noalloc.cu", "nrc_batch.cu", "nrc_serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -59,7 +59,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + f".tmp{os.getpid()}"
-    res = subprocess.run([cc, "-shared", "-o", tmp] + objs + ARCH + ["-Xcompiler", "-fPIC"], capture_output=True,
+    res = subprocess.run([cc, "-shared", "-o", tmp] + objs + ARCH + ["-Xcompiler", "-fPIC", "-lpthread"], capture_output=True,
                          text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")

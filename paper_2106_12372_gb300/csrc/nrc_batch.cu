@@ -7,33 +7,9 @@
 #include <new>
 #include <vector>
 
-#include "nrc_internal.cuh"
+#include "batch.cuh"
 
 namespace nrc {
-
-constexpr int kRing = 8;  // pinned descriptor slots in flight
-
-struct Batch {
-  std::vector<nrc_cache*> caches;
-  int unit_tiles = 20;
-  int max_units = 0;
-  int max_jobs = 0;
-  // device
-  BatchCache* d_caches = nullptr;
-  BatchUnit* d_units = nullptr;
-  unsigned* d_counter = nullptr;
-  TrainJob* d_jobs = nullptr;
-  AdamJob* d_adam = nullptr;
-  float* d_partials = nullptr;
-  // host: last uploaded query descriptors, pinned staging ring
-  std::vector<BatchCache> h_caches;
-  std::vector<BatchUnit> h_units;
-  uint8_t* pinned = nullptr;
-  size_t slot_bytes = 0;
-  cudaEvent_t ev[kRing] = {};
-  int ring = 0;
-  int sm_count = 0;
-};
 
 static size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -46,19 +22,31 @@ static uint8_t* ring_slot(Batch* b, int* idx) {
   return b->pinned + size_t(i) * b->slot_bytes;
 }
 
-static bool same_cfg(const nrc_config& a, const nrc_config& b) {
+bool batch_same_cfg(const nrc_config& a, const nrc_config& b) {
   return a.width == b.width && a.hidden_layers == b.hidden_layers && a.dtype == b.dtype && a.enc_mode == b.enc_mode &&
          a.loss_mode == b.loss_mode && a.pad_value == b.pad_value && a.lr == b.lr && a.beta1 == b.beta1 &&
          a.beta2 == b.beta2 && a.adam_eps == b.adam_eps && a.loss_eps == b.loss_eps;
 }
 
-}  // namespace nrc
+nrc_status batch_check(nrc_cache* const* caches, int n_caches) {
+  for (int c = 0; c < n_caches; ++c) {
+    if (!caches[c]) return set_error("batched caches: cache %d is NULL", c), NRC_ERR_INVALID_ARG;
+    if (caches[c]->cfg.dtype == NRC_FP32)
+      return set_error("batched caches compute in FP16 or BF16"), NRC_ERR_UNSUPPORTED;
+    if (!batch_same_cfg(caches[c]->cfg, caches[0]->cfg))
+      return set_error("batched caches: cache %d differs in configuration from cache 0", c), NRC_ERR_INVALID_ARG;
+    if (caches[c]->device != caches[0]->device)
+      return set_error("batched caches live on different devices"), NRC_ERR_INVALID_ARG;
+  }
+  return NRC_OK;
+}
 
-struct nrc_batch : nrc::Batch {};
+static size_t slot_size(const Batch* b) {
+  return up256(sizeof(BatchCache) * b->max_caches) + up256(sizeof(BatchUnit) * b->max_units) +
+         up256(sizeof(TrainJob) * b->max_jobs) + up256(sizeof(AdamJob) * b->max_caches);
+}
 
-using namespace nrc;
-
-static void free_batch(nrc_batch* b) {
+void batch_free(Batch* b) {
   cudaFree(b->d_caches);
   cudaFree(b->d_units);
   cudaFree(b->d_counter);
@@ -68,81 +56,82 @@ static void free_batch(nrc_batch* b) {
   cudaFreeHost(b->pinned);
   for (int i = 0; i < kRing; ++i)
     if (b->ev[i]) cudaEventDestroy(b->ev[i]);
-  delete b;
+  b->d_caches = nullptr;
+  b->d_units = nullptr;
+  b->d_counter = nullptr;
+  b->d_jobs = nullptr;
+  b->d_adam = nullptr;
+  b->d_partials = nullptr;
+  b->pinned = nullptr;
+  for (int i = 0; i < kRing; ++i) b->ev[i] = nullptr;
 }
 
-extern "C" {
-
-nrc_status nrc_batch_create(nrc_cache* const* caches, int32_t n_caches, nrc_batch** out) {
-  if (!out || !caches || n_caches <= 0) return set_error("nrc_batch_create: no caches"), NRC_ERR_INVALID_ARG;
-  *out = nullptr;
-  for (int c = 0; c < n_caches; ++c) {
-    if (!caches[c]) return set_error("nrc_batch_create: cache %d is NULL", c), NRC_ERR_INVALID_ARG;
-    if (caches[c]->cfg.dtype == NRC_FP32)
-      return set_error("nrc_batch_create: batched caches compute in FP16 or BF16"), NRC_ERR_UNSUPPORTED;
-    if (!same_cfg(caches[c]->cfg, caches[0]->cfg))
-      return set_error("nrc_batch_create: cache %d differs in configuration from cache 0", c), NRC_ERR_INVALID_ARG;
-    if (caches[c]->device != caches[0]->device)
-      return set_error("nrc_batch_create: caches live on different devices"), NRC_ERR_INVALID_ARG;
-  }
-  nrc_batch* b = new (std::nothrow) nrc_batch();
-  if (!b) return set_error("host allocation failed"), NRC_ERR_OOM;
-  b->caches.assign(caches, caches + n_caches);
-  b->sm_count = caches[0]->sm_count;
+nrc_status batch_init(Batch* b, const nrc_cache* proto, int max_caches) {
+  b->sm_count = proto->sm_count;
+  b->max_caches = max_caches;
   b->max_jobs = b->sm_count;
   b->max_units = 1 << 16;
-  const size_t stride = partial_stride(caches[0]->net.n_params);
-  b->slot_bytes = up256(sizeof(BatchCache) * n_caches) + up256(sizeof(BatchUnit) * b->max_units) +
-                  up256(sizeof(TrainJob) * b->max_jobs) + up256(sizeof(AdamJob) * n_caches);
-  cudaError_t e = cudaMalloc(&b->d_caches, sizeof(BatchCache) * n_caches);
+  b->stride = partial_stride(proto->net.n_params);
+  b->slot_bytes = slot_size(b);
+  cudaError_t e = cudaMalloc(&b->d_caches, sizeof(BatchCache) * max_caches);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_units, sizeof(BatchUnit) * b->max_units);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMalloc(&b->d_jobs, sizeof(TrainJob) * b->max_jobs);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_adam, sizeof(AdamJob) * n_caches);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_partials, size_t(b->max_jobs) * stride * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_adam, sizeof(AdamJob) * max_caches);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_partials, size_t(b->max_jobs) * b->stride * 4);
   if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&b->pinned), b->slot_bytes * kRing, cudaHostAllocDefault);
   for (int i = 0; i < kRing && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&b->ev[i], cudaEventDisableTiming);
   if (e != cudaSuccess) {
-    nrc_status s = cuda_status(e, "nrc_batch_create");
-    free_batch(b);
+    nrc_status s = cuda_status(e, "batched caches: allocation");
+    batch_free(b);
     return s;
   }
-  *out = b;
   return NRC_OK;
 }
 
-nrc_status nrc_batch_destroy(nrc_batch* b) {
-  if (!b) return NRC_OK;
-  cudaError_t e = cudaDeviceSynchronize();
-  free_batch(b);
-  return cuda_status(e, "nrc_batch_destroy");
-}
-
-nrc_status nrc_batch_set_unit_tiles(nrc_batch* b, int32_t unit_tiles) {
-  if (!b || unit_tiles < 1 || unit_tiles > 4096) return set_error("unit_tiles must be in [1, 4096]"), NRC_ERR_INVALID_ARG;
-  b->unit_tiles = unit_tiles;
+// Room for n_jobs training CTAs.  Growing waits for the work in flight on st
+// (the only stream these buffers are used on) and for the pinned ring.
+static nrc_status reserve_jobs(Batch* b, int n_jobs, cudaStream_t st) {
+  if (n_jobs <= b->max_jobs) return NRC_OK;
+  cudaError_t e = cudaStreamSynchronize(st);
+  for (int i = 0; i < kRing && e == cudaSuccess; ++i) e = cudaEventSynchronize(b->ev[i]);
+  if (e != cudaSuccess) return cuda_status(e, "batched training: growing the job buffers");
+  cudaFree(b->d_jobs);
+  cudaFree(b->d_partials);
+  cudaFreeHost(b->pinned);
+  b->d_jobs = nullptr;
+  b->d_partials = nullptr;
+  b->pinned = nullptr;
+  b->max_jobs = n_jobs;
+  b->slot_bytes = slot_size(b);
+  e = cudaMalloc(&b->d_jobs, sizeof(TrainJob) * b->max_jobs);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_partials, size_t(b->max_jobs) * b->stride * 4);
+  if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&b->pinned), b->slot_bytes * kRing, cudaHostAllocDefault);
+  if (e != cudaSuccess) {
+    b->max_jobs = 0;
+    return cuda_status(e, "batched training: growing the job buffers");
+  }
   return NRC_OK;
 }
 
-nrc_status nrc_batch_infer(nrc_batch* b, const float* const* records, const int64_t* n, float* const* rgb,
-                           nrc_stream stream) {
-  if (!b || !records || !n || !rgb) return set_error("nrc_batch_infer: NULL argument"), NRC_ERR_INVALID_ARG;
-  const int nc = int(b->caches.size());
+nrc_status batch_infer(Batch* b, nrc_cache* const* caches, int nc, const float* const* records, const int64_t* n,
+                       float* const* rgb, cudaStream_t st) {
+  if (!records || !n || !rgb) return set_error("batched query: NULL argument"), NRC_ERR_INVALID_ARG;
+  if (nc > b->max_caches) return set_error("batched query: %d caches, capacity %d", nc, b->max_caches), NRC_ERR_INVALID_ARG;
   std::vector<BatchCache> hc(static_cast<size_t>(nc));
   std::vector<BatchUnit> hu;
   for (int c = 0; c < nc; ++c) {
-    if (n[c] < 0) return set_error("nrc_batch_infer: n[%d] < 0", c), NRC_ERR_INVALID_ARG;
+    if (n[c] < 0) return set_error("batched query: n[%d] < 0", c), NRC_ERR_INVALID_ARG;
     if (n[c] > 0 && (!records[c] || !rgb[c] || (reinterpret_cast<uintptr_t>(records[c]) & 15u)))
-      return set_error("nrc_batch_infer: buffers of cache %d NULL or misaligned", c), NRC_ERR_INVALID_ARG;
-    if (n[c] > (int64_t(1) << 38)) return set_error("nrc_batch_infer: n[%d] too large", c), NRC_ERR_INVALID_ARG;
-    hc[c] = BatchCache{b->caches[c]->wimg, records[c], rgb[c], n[c]};
+      return set_error("batched query: buffers of cache %d NULL or misaligned", c), NRC_ERR_INVALID_ARG;
+    if (n[c] > (int64_t(1) << 38)) return set_error("batched query: n[%d] too large", c), NRC_ERR_INVALID_ARG;
+    hc[c] = BatchCache{caches[c]->wimg, records[c], rgb[c], n[c]};
     const int64_t tiles = (n[c] + kTile - 1) / kTile;
     for (int64_t t = 0; t < tiles; t += b->unit_tiles)
       hu.push_back(BatchUnit{c, int(t), int(std::min<int64_t>(tiles, t + b->unit_tiles))});
   }
   if (hu.empty()) return NRC_OK;
-  if (int(hu.size()) > b->max_units) return set_error("nrc_batch_infer: too many work units"), NRC_ERR_INVALID_ARG;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (int(hu.size()) > b->max_units) return set_error("batched query: too many work units"), NRC_ERR_INVALID_ARG;
   cudaError_t e = cudaSuccess;
   const bool same = hc.size() == b->h_caches.size() && hu.size() == b->h_units.size() &&
                     !std::memcmp(hc.data(), b->h_caches.data(), sizeof(BatchCache) * hc.size()) &&
@@ -151,55 +140,63 @@ nrc_status nrc_batch_infer(nrc_batch* b, const float* const* records, const int6
     int slot;
     uint8_t* h = ring_slot(b, &slot);
     std::memcpy(h, hc.data(), sizeof(BatchCache) * nc);
-    uint8_t* hu_p = h + up256(sizeof(BatchCache) * nc);
+    uint8_t* hu_p = h + up256(sizeof(BatchCache) * b->max_caches);
     std::memcpy(hu_p, hu.data(), sizeof(BatchUnit) * hu.size());
     e = cudaMemcpyAsync(b->d_caches, h, sizeof(BatchCache) * nc, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_units, hu_p, sizeof(BatchUnit) * hu.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaEventRecord(b->ev[slot], st);
-    if (e != cudaSuccess) return cuda_status(e, "nrc_batch_infer upload");
+    if (e != cudaSuccess) return cuda_status(e, "batched query: descriptor upload");
     b->h_caches = hc;
     b->h_units = hu;
   }
   const int grid = std::min<int>(b->sm_count, int(hu.size()));
-  e = launch_infer_batched(b->caches[0], b->d_caches, b->d_units, int(hu.size()), b->d_counter, grid, st);
-  for (auto* c : b->caches) c->launches += 1;
-  return cuda_status(e, "nrc_batch_infer");
+  e = launch_infer_batched(caches[0], b->d_caches, b->d_units, int(hu.size()), b->d_counter, grid, st);
+  for (int c = 0; c < nc; ++c) caches[c]->launches += 1;
+  return cuda_status(e, "batched query");
 }
 
-nrc_status nrc_batch_train_step(nrc_batch* b, const float* const* pool, const float* const* target,
-                                const int64_t* n_pool, const int64_t* batch, const uint64_t* frame_seed,
-                                int32_t step, float* const* loss_out, nrc_stream stream) {
-  if (!b || !pool || !target || !n_pool || !batch || !frame_seed || step < 0)
-    return set_error("nrc_batch_train_step: NULL argument or negative step"), NRC_ERR_INVALID_ARG;
-  const int nc = int(b->caches.size());
-  const size_t stride = partial_stride(b->caches[0]->net.n_params);
+nrc_status batch_train_step(Batch* b, nrc_cache* const* caches, int nc, const float* const* pool,
+                            const float* const* target, const int64_t* n_pool, const int64_t* batch,
+                            const uint64_t* frame_seed, int32_t step, float* const* loss_out, cudaStream_t st) {
+  if (!pool || !target || !n_pool || !batch || !frame_seed || step < 0)
+    return set_error("batched training: NULL argument or negative step"), NRC_ERR_INVALID_ARG;
+  if (nc > b->max_caches) return set_error("batched training: %d caches, capacity %d", nc, b->max_caches), NRC_ERR_INVALID_ARG;
   std::vector<int64_t> tiles(size_t(nc), 0);
   int64_t total = 0;
   for (int c = 0; c < nc; ++c) {
-    if (batch[c] < 0 || batch[c] > kMaxBatch) return set_error("nrc_batch_train_step: batch[%d] out of range", c), NRC_ERR_INVALID_ARG;
+    if (batch[c] < 0 || batch[c] > kMaxBatch) return set_error("batched training: batch[%d] out of range", c), NRC_ERR_INVALID_ARG;
     if (batch[c] == 0) continue;
     if (n_pool[c] >= (int64_t(1) << 31) || (int64_t(step) + 1) * batch[c] > n_pool[c])
-      return set_error("nrc_batch_train_step: (step+1)*batch[%d] exceeds n_pool or n_pool too large", c), NRC_ERR_INVALID_ARG;
+      return set_error("batched training: (step+1)*batch[%d] exceeds n_pool or n_pool too large", c), NRC_ERR_INVALID_ARG;
     if (!pool[c] || !target[c] || (reinterpret_cast<uintptr_t>(pool[c]) & 15u))
-      return set_error("nrc_batch_train_step: buffers of cache %d NULL or misaligned", c), NRC_ERR_INVALID_ARG;
+      return set_error("batched training: buffers of cache %d NULL or misaligned", c), NRC_ERR_INVALID_ARG;
     tiles[c] = (batch[c] + kTile - 1) / kTile;
     total += tiles[c];
   }
   if (total == 0) return NRC_OK;
-  // CTAs per cache in proportion to its tiles (at least one each), at most one per SM in all
-  const int budget = std::max(nc, b->max_jobs);
   std::vector<int> k(size_t(nc), 0);
   int used = 0;
-  for (int c = 0; c < nc; ++c)
-    if (tiles[c]) {
-      k[c] = int(std::max<int64_t>(1, std::min<int64_t>(tiles[c], budget * tiles[c] / total)));
+  if (b->train_tiles > 0) {  // each cache's CTA count from its own batch alone
+    for (int c = 0; c < nc; ++c) {
+      k[c] = int((tiles[c] + b->train_tiles - 1) / b->train_tiles);
       used += k[c];
     }
-  while (used > b->max_jobs) {  // trim the largest shares
-    int cmax = int(std::max_element(k.begin(), k.end()) - k.begin());
-    if (k[cmax] <= 1) return set_error("nrc_batch_train_step: more caches than CTAs"), NRC_ERR_UNSUPPORTED;
-    --k[cmax];
-    --used;
+    nrc_status s = reserve_jobs(b, used, st);
+    if (s != NRC_OK) return s;
+  } else {  // CTAs per cache in proportion to its tiles (at least one each), at most one per SM in all
+    const int budget = std::max(nc, b->sm_count);
+    nrc_status s = reserve_jobs(b, budget, st);
+    if (s != NRC_OK) return s;
+    for (int c = 0; c < nc; ++c)
+      if (tiles[c]) {
+        k[c] = int(std::max<int64_t>(1, std::min<int64_t>(tiles[c], budget * tiles[c] / total)));
+        used += k[c];
+      }
+    while (used > budget) {  // trim the largest shares
+      int cmax = int(std::max_element(k.begin(), k.end()) - k.begin());
+      --k[cmax];
+      --used;
+    }
   }
   int slot;
   uint8_t* h = ring_slot(b, &slot);
@@ -208,7 +205,7 @@ nrc_status nrc_batch_train_step(nrc_batch* b, const float* const* pool, const fl
   int j = 0, n_adam = 0;
   for (int c = 0; c < nc; ++c) {
     if (!tiles[c]) continue;
-    nrc_cache* cc = b->caches[c];
+    nrc_cache* cc = caches[c];
     uint64_t a, ic;
     lcg_params(n_pool[c], frame_seed[c], &a, &ic);
     const int j0 = j;
@@ -225,22 +222,81 @@ nrc_status nrc_batch_train_step(nrc_batch* b, const float* const* pool, const fl
       J.tile_end = int(tiles[c] * (q + 1) / k[c]);
       J.tile_step = 1;
       J.wimg = cc->wimg;
-      J.partial = b->d_partials + size_t(j) * stride;
+      J.partial = b->d_partials + size_t(j) * b->stride;
       J.t_ctr = cc->t;
       J.bump_t = q == 0;
       J.inv3n = float(1.0 / (3.0 * double(batch[c])));
     }
-    ha[n_adam++] = AdamJob{cc->w, cc->m, cc->v, cc->t, b->d_partials + size_t(j0) * stride, k[c], cc->wimg,
+    ha[n_adam++] = AdamJob{cc->w, cc->m, cc->v, cc->t, b->d_partials + size_t(j0) * b->stride, k[c], cc->wimg,
                            float(1.0 / (3.0 * double(batch[c]))), loss_out ? loss_out[c] : nullptr};
   }
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemcpyAsync(b->d_jobs, hj, sizeof(TrainJob) * j, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_adam, ha, sizeof(AdamJob) * n_adam, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaEventRecord(b->ev[slot], st);
-  if (e == cudaSuccess) e = launch_train_batched(b->caches[0], b->d_jobs, j, st);
-  if (e == cudaSuccess) e = launch_adam_batched(b->caches[0], b->d_adam, n_adam, st);
-  for (auto* c : b->caches) c->launches += 2;
-  return cuda_status(e, "nrc_batch_train_step");
+  if (e == cudaSuccess) e = launch_train_batched(caches[0], b->d_jobs, j, st);
+  if (e == cudaSuccess) e = launch_adam_batched(caches[0], b->d_adam, n_adam, st);
+  for (int c = 0; c < nc; ++c) caches[c]->launches += 2;
+  return cuda_status(e, "batched training");
+}
+
+}  // namespace nrc
+
+struct nrc_batch : nrc::Batch {};
+
+using namespace nrc;
+
+extern "C" {
+
+nrc_status nrc_batch_create(nrc_cache* const* caches, int32_t n_caches, nrc_batch** out) {
+  if (!out || !caches || n_caches <= 0) return set_error("nrc_batch_create: no caches"), NRC_ERR_INVALID_ARG;
+  *out = nullptr;
+  nrc_status s = batch_check(caches, n_caches);
+  if (s != NRC_OK) return s;
+  nrc_batch* b = new (std::nothrow) nrc_batch();
+  if (!b) return set_error("host allocation failed"), NRC_ERR_OOM;
+  b->caches.assign(caches, caches + n_caches);
+  s = batch_init(b, caches[0], n_caches);
+  if (s != NRC_OK) {
+    delete b;
+    return s;
+  }
+  *out = b;
+  return NRC_OK;
+}
+
+nrc_status nrc_batch_destroy(nrc_batch* b) {
+  if (!b) return NRC_OK;
+  cudaError_t e = cudaDeviceSynchronize();
+  batch_free(b);
+  delete b;
+  return cuda_status(e, "nrc_batch_destroy");
+}
+
+nrc_status nrc_batch_set_unit_tiles(nrc_batch* b, int32_t unit_tiles) {
+  if (!b || unit_tiles < 1 || unit_tiles > 4096) return set_error("unit_tiles must be in [1, 4096]"), NRC_ERR_INVALID_ARG;
+  b->unit_tiles = unit_tiles;
+  return NRC_OK;
+}
+
+nrc_status nrc_batch_set_train_tiles(nrc_batch* b, int32_t train_tiles) {
+  if (!b || train_tiles < 0 || train_tiles > 4096) return set_error("train_tiles must be in [0, 4096]"), NRC_ERR_INVALID_ARG;
+  b->train_tiles = train_tiles;
+  return NRC_OK;
+}
+
+nrc_status nrc_batch_infer(nrc_batch* b, const float* const* records, const int64_t* n, float* const* rgb,
+                           nrc_stream stream) {
+  if (!b) return set_error("nrc_batch_infer: batch is NULL"), NRC_ERR_INVALID_ARG;
+  return batch_infer(b, b->caches.data(), int(b->caches.size()), records, n, rgb,
+                     reinterpret_cast<cudaStream_t>(stream));
+}
+
+nrc_status nrc_batch_train_step(nrc_batch* b, const float* const* pool, const float* const* target,
+                                const int64_t* n_pool, const int64_t* batch, const uint64_t* frame_seed,
+                                int32_t step, float* const* loss_out, nrc_stream stream) {
+  if (!b) return set_error("nrc_batch_train_step: batch is NULL"), NRC_ERR_INVALID_ARG;
+  return batch_train_step(b, b->caches.data(), int(b->caches.size()), pool, target, n_pool, batch, frame_seed, step,
+                          loss_out, reinterpret_cast<cudaStream_t>(stream));
 }
 
 nrc_status nrc_batch_autotune(nrc_batch* b, const float* const* records, const int64_t* n, float* const* rgb,

@@ -18,7 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libnrc.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "nrc.h")
 
-NRC_OK, NRC_ERR_INVALID_ARG, NRC_ERR_CUDA, NRC_ERR_OOM, NRC_ERR_TIMEOUT, NRC_ERR_UNSUPPORTED = range(6)
+NRC_OK, NRC_ERR_INVALID_ARG, NRC_ERR_CUDA, NRC_ERR_OOM, NRC_ERR_TIMEOUT, NRC_ERR_UNSUPPORTED, NRC_ERR_BUSY = range(7)
 FP32, FP16, BF16 = 0, 1, 2
 ENC_CHEAP, ENC_EXACT = 0, 1
 LOSS_LUMINANCE, LOSS_PER_CHANNEL = 0, 1
@@ -50,6 +50,46 @@ class Config(ctypes.Structure):
         ("adam_eps", ctypes.c_float),
         ("loss_eps", ctypes.c_float),
         ("seed", ctypes.c_uint64),
+    ]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [
+        ("memory_budget", ctypes.c_uint64),
+        ("max_viewports", ctypes.c_int32),
+        ("max_inflight", ctypes.c_int32),
+        ("train_steps", ctypes.c_int32),
+        ("train_batch", ctypes.c_int32),
+        ("train_tiles", ctypes.c_int32),
+        ("unit_tiles", ctypes.c_int32),
+    ]
+
+
+class FrameDone(ctypes.Structure):
+    _fields_ = [
+        ("viewport", ctypes.c_int32),
+        ("slot", ctypes.c_int32),
+        ("tag", ctypes.c_int64),
+        ("n_queries", ctypes.c_int64),
+        ("arrival_ns", ctypes.c_int64),
+        ("submit_ns", ctypes.c_int64),
+        ("launch_ns", ctypes.c_int64),
+        ("done_ns", ctypes.c_int64),
+        ("batch_frames", ctypes.c_int32),
+        ("failed", ctypes.c_int32),
+    ]
+
+
+class ServerInfo(ctypes.Structure):
+    _fields_ = [
+        ("memory_used", ctypes.c_uint64),
+        ("memory_budget", ctypes.c_uint64),
+        ("frames_done", ctypes.c_int64),
+        ("batches", ctypes.c_int64),
+        ("queries_done", ctypes.c_int64),
+        ("pending", ctypes.c_int64),
+        ("viewports", ctypes.c_int32),
+        ("inflight", ctypes.c_int32),
     ]
 
 
@@ -93,6 +133,19 @@ def lib() -> ctypes.CDLL:
             "nrc_batch_train_step": (i32, [P, P, P, P, P, P, i32, P, P]),
             "nrc_batch_set_unit_tiles": (i32, [P, i32]),
             "nrc_batch_autotune": (i32, [P, P, P, P, P, P]),
+            "nrc_batch_set_train_tiles": (i32, [P, i32]),
+            "nrc_server_default_config": (None, [P]),
+            "nrc_now_ns": (i64, []),
+            "nrc_server_create": (i32, [P, P, P]),
+            "nrc_server_destroy": (i32, [P]),
+            "nrc_server_open_viewport": (i32, [P, P, i64, i64, i32, P]),
+            "nrc_server_close_viewport": (i32, [P, i32]),
+            "nrc_server_viewport_buffers": (i32, [P, i32, i32, P, P, P]),
+            "nrc_server_viewport_pool": (i32, [P, i32, P, P, P]),
+            "nrc_server_submit": (i32, [P, i32, i32, i64, u64, i64, i64]),
+            "nrc_server_poll": (i32, [P, P, i32, i32, P]),
+            "nrc_server_drain": (i32, [P]),
+            "nrc_server_query": (i32, [P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -287,9 +340,125 @@ class Batch:
     def set_unit_tiles(self, u: int) -> None:
         _check(lib().nrc_batch_set_unit_tiles(self._h, u))
 
+    def set_train_tiles(self, t: int) -> None:
+        _check(lib().nrc_batch_set_train_tiles(self._h, t))
+
     def autotune(self, records, rgb, stream=None) -> int:
         n = (ctypes.c_int64 * len(records))(*[r.shape[0] for r in records])
         chosen = ctypes.c_int32()
         _check(lib().nrc_batch_autotune(self._h, _ptr_array(records), n, _ptr_array(rgb), _stream(stream),
                                         ctypes.byref(chosen)))
         return chosen.value
+
+
+class _BorrowedCache(Cache):
+    """A cache handle owned elsewhere (a server's viewport): never destroyed from here."""
+
+    def __init__(self, handle: int):
+        self._h = ctypes.c_void_p(handle)
+
+    def close(self) -> None:
+        self._h = None
+
+
+class _DeviceView:
+    """A float32 device buffer owned by the library, viewable as a torch tensor."""
+
+    def __init__(self, ptr: int, shape: tuple):
+        self.__cuda_array_interface__ = {"shape": shape, "typestr": "<f4", "data": (ptr, False), "version": 2,
+                                         "strides": None}
+
+
+def _view(ptr: int, shape: tuple):
+    import torch
+
+    return torch.as_tensor(_DeviceView(ptr, shape), device="cuda")
+
+
+def now_ns() -> int:
+    return lib().nrc_now_ns()
+
+
+class Server:
+    """Continuous-batching server of several viewports' caches (see include/nrc.h)."""
+
+    def __init__(self, cache_cfg: Config | None = None, **kw):
+        cfg = ServerConfig()
+        lib().nrc_server_default_config(ctypes.byref(cfg))
+        for k, v in kw.items():
+            setattr(cfg, k, v)
+        self.cfg = cfg
+        self.cache_cfg = cache_cfg if cache_cfg is not None else default_config(dtype="fp16")
+        h = ctypes.c_void_p()
+        _check(lib().nrc_server_create(ctypes.byref(cfg), ctypes.byref(self.cache_cfg), ctypes.byref(h)))
+        self._h = h
+        self._vp = {}
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            h, self._h = self._h, None
+            _check(lib().nrc_server_destroy(h))
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def open_viewport(self, max_queries: int, n_pool: int, n_slots: int = 2, seed: int | None = None) -> int:
+        """Admits a viewport (raises NrcError with status NRC_ERR_BUSY if it does not fit the budget)."""
+        c = Config.from_buffer_copy(self.cache_cfg)
+        if seed is not None:
+            c.seed = seed
+        vid = ctypes.c_int32()
+        _check(lib().nrc_server_open_viewport(self._h, ctypes.byref(c), max_queries, n_pool, n_slots,
+                                              ctypes.byref(vid)))
+        self._vp[vid.value] = (max_queries, n_pool, n_slots)
+        return vid.value
+
+    def close_viewport(self, vid: int) -> None:
+        _check(lib().nrc_server_close_viewport(self._h, vid))
+        self._vp.pop(vid, None)
+
+    def buffers(self, vid: int, slot: int):
+        """(records [max_queries,16], rgb [max_queries,3], losses [train_steps]) of a slot, as device tensors."""
+        r, g, l = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        _check(lib().nrc_server_viewport_buffers(self._h, vid, slot, ctypes.byref(r), ctypes.byref(g),
+                                                 ctypes.byref(l)))
+        mq = self._vp[vid][0]
+        return (_view(r.value, (mq, 16)), _view(g.value, (mq, 3)), _view(l.value, (max(1, self.cfg.train_steps),)))
+
+    def pool(self, vid: int):
+        """(pool [n_pool,16], target [n_pool,3]) device tensors and the viewport's cache handle."""
+        p, t, c = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        _check(lib().nrc_server_viewport_pool(self._h, vid, ctypes.byref(p), ctypes.byref(t), ctypes.byref(c)))
+        n = self._vp[vid][1]
+        return _view(p.value, (n, 16)), _view(t.value, (n, 3)), c.value
+
+    def cache(self, vid: int) -> "Cache":
+        """The viewport's cache (owned by the server; use get_state / set_state after drain)."""
+        return _BorrowedCache(self.pool(vid)[2])
+
+    def submit(self, vid: int, slot: int, n_queries: int, frame_seed: int, arrival_ns: int | None = None,
+               tag: int = 0) -> bool:
+        """Queues a frame; False if the slot's previous frame is still in flight."""
+        st = lib().nrc_server_submit(self._h, vid, slot, n_queries, frame_seed & (2**64 - 1),
+                                     now_ns() if arrival_ns is None else arrival_ns, tag)
+        if st == NRC_ERR_BUSY:
+            return False
+        _check(st)
+        return True
+
+    def poll(self, max_out: int = 256, timeout_ms: int = 0) -> list:
+        buf = (FrameDone * max_out)()
+        n = ctypes.c_int32()
+        _check(lib().nrc_server_poll(self._h, buf, max_out, timeout_ms, ctypes.byref(n)))
+        return [buf[i] for i in range(n.value)]
+
+    def drain(self) -> None:
+        _check(lib().nrc_server_drain(self._h))
+
+    def info(self) -> ServerInfo:
+        out = ServerInfo()
+        _check(lib().nrc_server_query(self._h, ctypes.byref(out)))
+        return out
