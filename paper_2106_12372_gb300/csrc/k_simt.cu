@@ -440,17 +440,20 @@ __device__ __forceinline__ void adam_block(float* __restrict__ w, float* __restr
   }
   float part = 0.0f;
   if (p < net.n_params) {
+    // 16 independent loads in flight per thread (the partials were just
+    // written and sit in L2; latency, not bandwidth, bounds this loop)
     const float* src = partials + p;
     int k = grp;
-    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
-    for (; k + 3 * kAdamGroups < n_partials; k += 4 * kAdamGroups) {
-      a0 += src[size_t(k) * stride];
-      a1 += src[size_t(k + kAdamGroups) * stride];
-      a2 += src[size_t(k + 2 * kAdamGroups) * stride];
-      a3 += src[size_t(k + 3 * kAdamGroups) * stride];
+    float a[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (; k + 15 * kAdamGroups < n_partials; k += 16 * kAdamGroups) {
+      float t[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) t[u] = __ldcg(src + size_t(k + u * kAdamGroups) * stride);
+#pragma unroll
+      for (int u = 0; u < 16; ++u) a[u & 3] += t[u];
     }
-    for (; k < n_partials; k += kAdamGroups) a0 += src[size_t(k) * stride];
-    part = (a0 + a1) + (a2 + a3);
+    for (; k < n_partials; k += kAdamGroups) a[0] += __ldcg(src + size_t(k) * stride);
+    part = (a[0] + a[1]) + (a[2] + a[3]);
   }
   red[grp][lane] = part;
   __syncthreads();

@@ -499,7 +499,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(const __grid_cons
   __shared__ float red[4];
   uint8_t* sw = align1024(smem_raw);                 // weight image
   uint8_t* Hs = sw + ((p.img_bytes + 1023) & ~1023); // n_mats x 16 KB
-  uint8_t* Ds = Hs + p.n_mats * 16384;               // 16 KB
+  uint8_t* Ds = Hs + p.n_mats * 16384;               // 2 x 16 KB (delta of layer l in buffer l % 2)
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
   const int half = tid >> 7;  // column half of this thread
@@ -524,6 +524,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(const __grid_cons
   const uint32_t t_acc = tmem + lane_base + uint32_t(32 * half);        // my 32 accumulator columns
   const uint32_t t_act = tmem + lane_base + 64 + uint32_t(16 * half);   // my 16 packed activation columns
   const uint32_t sw_base = smem_u32(sw), hs_base = smem_u32(Hs), ds_base = smem_u32(Ds);
+  auto ds_buf = [&](int l) { return Ds + (l & 1) * 16384; };
   const int L = p.n_mats;
   uint32_t phase = 0;
   float loss_acc = 0.0f;
@@ -553,28 +554,28 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(const __grid_cons
   // One dependent step: make this warpgroup pair's shared-memory and TMEM
   // writes visible, issue the MMAs (one thread), run `overlap` while they
   // execute, wait for them.
-  auto mma_stage = [&](auto&& issue, auto&& overlap) {
+  auto mma_stage = [&](auto&& issue, auto&& overlap, bool commit) {
     fence_proxy_async_smem();
     fence_before();
     named_sync(1, kTrainThreads);
     if (tid == 0) {
       fence_after();
       issue();
-      mma_commit(&bar_mma);
+      if (commit) mma_commit(&bar_mma);
     }
     overlap();
     mbar_wait(&bar_mma, phase, p.err);
     phase ^= 1u;
     fence_after();
   };
-  auto mma_sync_issue_wait = [&](auto&& issue) { mma_stage(issue, []() {}); };
+  auto mma_sync_issue_wait = [&](auto&& issue) { mma_stage(issue, []() {}, true); };
 
   // Weight-gradient write-out, overlapped with the backward pass of the CTA's
   // last tile: once dW_l is final and H_l is no longer needed, the threads
   // owning TMEM lanes 0..63 stage dW_l into H_l's buffer (row o at o*64 floats,
   // 16-byte chunk c of each 128-byte half at chunk c ^ (o % 8): conflict-free),
   // and after the next barrier all 256 threads copy it to the CTA's partial
-  // with coalesced stores.
+  // with coalesced 16-byte stores.
   float* P = J.partial;
   auto stage_dw = [&](int l) {
     if ((warp & 3) >= 2) return;
@@ -594,10 +595,10 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(const __grid_cons
   auto write_dw = [&](int l) {
     const int dout = (l + 1 < L) ? 64 : kOutDims;
     const float* S = reinterpret_cast<const float*>(Hs + l * 16384);
-    float* Pl = P + p.w_off[l];
-    for (int e = tid; e < dout * 64; e += kTrainThreads) {
-      const int o = e >> 6, i = e & 63;
-      Pl[e] = S[o * 64 + (i & 32) + ((((i >> 2) & 7) ^ (o & 7)) << 2) + (i & 3)];
+    float4* Pl = reinterpret_cast<float4*>(P + p.w_off[l]);
+    for (int e = tid; e < dout * 16; e += kTrainThreads) {
+      const int o = e >> 4, c = e & 15;  // 16-byte chunk c of row o: inputs 4c .. 4c+3
+      Pl[e] = *reinterpret_cast<const float4*>(S + o * 64 + (c & 8) * 4 + (((c & 7) ^ (o & 7)) << 2));
     }
   };
 
@@ -689,23 +690,21 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(const __grid_cons
       pk[0] = pack2<BF16, false>(g[0], g[1]);
       pk[1] = pack2<BF16, false>(g[2], 0.0f);
     }
-    store_half_row_sw128(Ds, r, 4 * half, pk);
+    store_half_row_sw128(ds_buf(L), r, 4 * half, pk);
     tmem_st16(t_act, pk);
     tmem_st_wait();
 
     // ----------------------------------------------------------- backward
+    // Stage l issues delta_l = (delta_{l+1} W_l) first and commits it alone:
+    // the epilogue waits for these 4 MMAs only, while dW_l (8 MMAs, issued
+    // after the commit) finishes in the background.  MMAs complete in issue
+    // order, so stage l's wait also covers every earlier stage's dW; dW_l
+    // reads delta_{l+1} from buffer (l+1) % 2 while the epilogue writes
+    // delta_l into the other one.
     const bool last_tile = tile + J.tile_step >= J.tile_end;
     for (int l = L - 1; l >= 0; --l) {
       const bool first_acc = first;
       mma_stage([&]() {
-        // dW_l (+)= delta_{l+1}^T H_l over this tile's 128 rows
-        const uint32_t idw = idesc_f16(128, 64, BF16, true, true);
-        const uint32_t dcol = tmem + 128 + uint32_t(l * 64);
-        const uint32_t hb = hs_base + uint32_t(l * 16384);
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-          mma_ss(dcol, sdesc_sw128(ds_base + uint32_t(k * 2048), 0, 1024),
-                 sdesc_sw128(hb + uint32_t(k * 2048), 1024, 1024), idw, (first_acc && k == 0) ? 0u : 1u);
         if (l > 0) {
           // delta_l (pre-mask) = delta_{l+1} W_l: K = rows of W_l (64, or 16 for the output layer)
           const int K = p.img.rows[l];
@@ -714,13 +713,24 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(const __grid_cons
           for (int k = 0; k < K / 16; ++k)
             mma_ts(tmem + 0, tmem + 64 + uint32_t(k * 8), sdesc_sw128(b0 + uint32_t(k * 2048), 1024, 1024), idd,
                    k > 0 ? 1u : 0u);
+          mma_commit(&bar_mma);
         }
+        // dW_l (+)= delta_{l+1}^T H_l over this tile's 128 rows
+        const uint32_t idw = idesc_f16(128, 64, BF16, true, true);
+        const uint32_t dcol = tmem + 128 + uint32_t(l * 64);
+        const uint32_t hb = hs_base + uint32_t(l * 16384);
+        const uint32_t db = ds_base + uint32_t(((l + 1) & 1) * 16384);
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          mma_ss(dcol, sdesc_sw128(db + uint32_t(k * 2048), 0, 1024), sdesc_sw128(hb + uint32_t(k * 2048), 1024, 1024),
+                 idw, (first_acc && k == 0) ? 0u : 1u);
+        if (l == 0) mma_commit(&bar_mma);  // the last stage waits for dW_0 as well
       }, [&]() {
         if (last_tile) {
-          if (l + 1 < L) stage_dw(l + 1);  // dW_{l+1} final since the previous stage; its mask read is done
-          if (l + 2 < L) write_dw(l + 2);  // staged during the previous stage, before this stage's barrier
+          if (l + 2 < L) stage_dw(l + 2);  // dW_{l+2} final since the previous stage's wait
+          if (l + 3 < L) write_dw(l + 3);  // staged during the previous stage, before this stage's barrier
         }
-      });
+      }, false);
       if (l == 0) break;
       uint32_t v[32], h2[16];
       tmem_ld32(t_acc, v);
@@ -728,7 +738,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(const __grid_cons
 #pragma unroll
       for (int q = 0; q < 16; ++q)
         pk[q] = masked_delta2<BF16>(__uint_as_float(v[2 * q]), __uint_as_float(v[2 * q + 1]), h2[q]);
-      store_half_row_sw128(Ds, r, 4 * half, pk);
+      store_half_row_sw128(ds_buf(l), r, 4 * half, pk);
       tmem_st16(t_act, pk);
       tmem_st_wait();
     }
@@ -739,8 +749,12 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(const __grid_cons
 
   // ------------------------------------------- the rest of the CTA's partial
   if (!first) {
-    stage_dw(0);  // dW_0 is final after the last backward stage (no epilogue reads H_0 there)
+    // dW_1 and dW_0 are final after the last backward stage (no epilogue reads
+    // H_1 or H_0 any more); dW_2 was staged during that stage
+    if (L >= 2) stage_dw(1);
+    stage_dw(0);
     __syncthreads();
+    if (L >= 3) write_dw(2);
     if (L >= 2) write_dw(1);
     write_dw(0);
   } else {  // a CTA without a tile contributes zeros
@@ -788,7 +802,7 @@ cudaError_t launch_train_tc(Cache* c, const float* pool, const float* target, in
   cudaError_t e = ensure_partials(c, grid);
   if (e != cudaSuccess) return e;
   p.partials = c->partials;
-  const int smem = ((p.img_bytes + 1023) & ~1023) + p.n_mats * 16384 + 16384 + 1024;
+  const int smem = ((p.img_bytes + 1023) & ~1023) + p.n_mats * 16384 + 2 * 16384 + 1024;
   const bool bf16 = c->cfg.dtype == NRC_BF16;
   const int mode = c->cfg.enc_mode;
   static int attr_done[4] = {0, 0, 0, 0};
@@ -839,7 +853,7 @@ cudaError_t launch_train_batched(const Cache* proto, const TrainJob* jobs, int n
   p.loss_mode = proto->cfg.loss_mode;
   p.loss_eps = proto->cfg.loss_eps;
   p.err = proto->err;
-  const int smem = ((p.img_bytes + 1023) & ~1023) + p.n_mats * 16384 + 16384 + 1024;
+  const int smem = ((p.img_bytes + 1023) & ~1023) + p.n_mats * 16384 + 2 * 16384 + 1024;
   const bool bf16 = proto->cfg.dtype == NRC_BF16;
   const int mode = proto->cfg.enc_mode;
   cudaLaunchConfig_t lc = {};
