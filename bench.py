@@ -92,6 +92,20 @@ def dist_env():
     return ws, rank, local
 
 
+def job_throughput(local_ms: float, units_per_rank: int, steps: int, ws: int, device=None):
+    """The timed region's length as the MAX over ranks, and whole-job throughput
+    in millions of units per second: the units all ranks processed over it."""
+    import torch
+
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    return total_ms, units_per_rank * steps * ws / (total_ms / 1e3) / 1e6
+
+
 def cpu_oracle_frame(budget_s: float, seed: int = 2106):
     """Times the FP64 oracle on a bounded sample of the frame; returns (Mqueries/s, description, cores)."""
     import numpy as np
@@ -376,12 +390,7 @@ def run_gpu(args):
     frame_ms = [e[0].elapsed_time(e[2]) for e in evs]
     infer_ms = [e[0].elapsed_time(e[1]) for e in evs]
     train_ms = [e[1].elapsed_time(e[2]) for e in evs]
-    total_ms = sum(frame_ms)
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = t.item()
-    value = N_QUERIES * args.steps * ws / (total_ms / 1e3) / 1e6
+    total_ms, value = job_throughput(sum(frame_ms), N_QUERIES, args.steps, ws, device=dev)
 
     # plain per-layer FP32 path on the same frame (a few frames; same cache shape)
     plain = nrc.Cache(dtype="fp32", path=nrc.PATH_PLAIN, seed=seed)
