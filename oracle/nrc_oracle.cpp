@@ -17,6 +17,8 @@
 //   * relative L2 loss, luminance normalisation              - Sec. 5, Eq. 5
 //   * backward pass and weight gradients                     - Sec. 4 "Training the fully fused network"
 //   * Adam                                                   - Sec. 5 "Optimizer" (Kingma & Ba 2015)
+//   * exponential moving average of the weights              - Sec. 3.3, Eq. 2 (as read below)
+//   * reflectance factorisation of the output                - Sec. 5 "Reflectance factorization"
 //
 // Readings where the paper is silent (each is listed in the design notes):
 //   * the shuffle is one affine map i -> (a*i + c) mod N with gcd(a, N) = 1,
@@ -27,7 +29,13 @@
 //     (quartic support radius 1/k; Gaussian standard deviation 1/k); no wrap;
 //   * luminance = Rec. 709 weights of the stop-gradient prediction; the loss
 //     is the mean over the 3*N channel terms;
-//   * Adam with bias correction, eps = 1e-8 unless given, no weight decay.
+//   * Adam with bias correction, eps = 1e-8 unless given, no weight decay;
+//   * Eq. 2 as printed is not an average (a constant sequence does not map to
+//     itself); it is read as the bias-corrected average the text describes,
+//     EMA_t = ((1 - a) W_t + a eta_{t-1} EMA_{t-1}) / eta_t, eta_t = 1 - a^t;
+//   * factorisation: the prediction is the network output times the sum of
+//     the record's diffuse and specular albedo, channel by channel; the loss
+//     compares that product with the target.
 //
 // Parity pins (what fixes each function other than itself) are in the tests.
 
@@ -91,7 +99,7 @@ uint64_t gcd_u64(uint64_t a, uint64_t b) {
 
 extern "C" {
 
-int oracle_abi_version() { return 1; }
+int oracle_abi_version() { return 2; }
 
 // ---------------------------------------------------------------- Sec. 3.5 --
 // The shuffle of the training records by a linear congruential generator,
@@ -328,25 +336,47 @@ void oracle_adam(double* W, double* m, double* v, const double* g, int64_t count
   }
 }
 
+// ------------------------------------------- Sec. 3.3, Eq. 2 (as read) -----
+// One update of the weight average after optimisation step t >= 1:
+// EMA_t = ((1 - alpha) W_t + alpha eta_{t-1} EMA_{t-1}) / eta_t with
+// eta_t = 1 - alpha^t (eta_0 = 0, so EMA_1 = W_1 whatever EMA_0 holds).
+void oracle_ema(double* ema, const double* W, int64_t count, int64_t t, double alpha) {
+  const double eta_t = 1.0 - std::pow(alpha, double(t));
+  const double eta_prev = 1.0 - std::pow(alpha, double(t - 1));
+  for (int64_t p = 0; p < count; ++p) ema[p] = ((1.0 - alpha) * W[p] + alpha * eta_prev * ema[p]) / eta_t;
+}
+
+// ------------------------------- Sec. 5 "Reflectance factorization" ---------
+// Multiplies each row's 3 outputs by the record's diffuse + specular albedo
+// (record floats 8..10 and 11..13), channel by channel.
+void oracle_factor(const float* rec, int64_t n, double* y) {
+  for (int64_t r = 0; r < n; ++r)
+    for (int ch = 0; ch < 3; ++ch)
+      y[r * 3 + ch] *= double(rec[r * kRecFloats + 8 + ch]) + double(rec[r * kRecFloats + 11 + ch]);
+}
+
 // ------------------------------------------------------------ composites ----
 // Inference (Sec. 3.1: the cache is queried at terminal vertices): encode,
 // then forward.
 void oracle_infer(const double* W, const int* dims, int n_mats, const float* rec, int64_t n, int enc_mode,
-                  double pad_value, double* y) {
+                  double pad_value, int refl_factor, double* y) {
   std::vector<double> x(static_cast<size_t>(n) * kEncDims);
   oracle_encode(rec, n, enc_mode, pad_value, x.data());
   oracle_forward(W, dims, n_mats, x.data(), n, y, nullptr);
+  if (refl_factor) oracle_factor(rec, n, y);
 }
 
 // One optimisation step (Sec. 3.3: several steps per frame, each on a disjoint
 // slice of the shuffled records): gather, encode, forward, loss, backward,
 // Adam.  W, m, v are updated in place; *t is incremented first (t counts
 // steps from 1).  Returns the loss of the batch before the update; grad (if
-// not null) receives dW.
+// not null) receives dW.  With refl_factor the loss compares the factorised
+// prediction y * f (f = diffuse + specular albedo) with the target, so the
+// gradient reaching the network output is dL/d(y f) * f.
 double oracle_train_step(double* W, double* m, double* v, int64_t* t, const int* dims, int n_mats, const float* pool,
                          const float* target, int64_t n_pool, int64_t batch, uint64_t frame_seed, int step,
                          int enc_mode, double pad_value, int loss_mode, double loss_eps, double lr, double b1,
-                         double b2, double adam_eps, double* grad) {
+                         double b2, double adam_eps, int refl_factor, double* grad) {
   std::vector<float> rec(static_cast<size_t>(batch) * kRecFloats);
   std::vector<float> tgt(static_cast<size_t>(batch) * 3);
   oracle_gather(pool, target, n_pool, batch, frame_seed, step, rec.data(), tgt.data(), nullptr);
@@ -358,7 +388,9 @@ double oracle_train_step(double* W, double* m, double* v, int64_t* t, const int*
   std::vector<double> y(static_cast<size_t>(batch) * dims[n_mats]);
   std::vector<double> g(static_cast<size_t>(batch) * dims[n_mats]);
   oracle_forward(W, dims, n_mats, x.data(), batch, y.data(), acts.data());
+  if (refl_factor) oracle_factor(rec.data(), batch, y.data());
   const double loss = oracle_loss(y.data(), tgt.data(), batch, loss_mode, loss_eps, g.data());
+  if (refl_factor) oracle_factor(rec.data(), batch, g.data());  // chain rule through y * f
   const int64_t n_par = w_offset(dims, n_mats);
   std::vector<double> dW(static_cast<size_t>(n_par));
   oracle_backward(W, dims, n_mats, acts.data(), g.data(), batch, dW.data());

@@ -61,9 +61,11 @@ def lib() -> ctypes.CDLL:
                 "oracle_loss": (f64, [P, P, i64, i32, f64, P]),
                 "oracle_backward": (None, [P, P, i32, P, P, i64, P]),
                 "oracle_adam": (None, [P, P, P, P, i64, i64, f64, f64, f64, f64]),
-                "oracle_infer": (None, [P, P, i32, P, i64, i32, f64, P]),
+                "oracle_infer": (None, [P, P, i32, P, i64, i32, f64, i32, P]),
                 "oracle_train_step": (f64, [P, P, P, P, P, i32, P, P, i64, i64, u64, i32, i32, f64, i32, f64,
-                                            f64, f64, f64, f64, P]),
+                                            f64, f64, f64, f64, i32, P]),
+                "oracle_ema": (None, [P, P, i64, i64, f64]),
+                "oracle_factor": (None, [P, i64, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -173,32 +175,51 @@ def adam(W, m, v, g, t: int, lr=1e-2, b1=0.9, b2=0.99, eps=1e-8):
     return W, m, v
 
 
-def infer(W, dims, rec, enc_mode: int = ENC_CHEAP, pad_value: float = 1.0) -> np.ndarray:
+def infer(W, dims, rec, enc_mode: int = ENC_CHEAP, pad_value: float = 1.0, refl_factor: bool = False) -> np.ndarray:
     W, d, rec = _f64(W), _dims(dims), _f32(rec).reshape(-1, 16)
     y = np.zeros((rec.shape[0], dims[-1]), dtype=np.float64)
-    lib().oracle_infer(_p(W), _p(d), len(dims) - 1, _p(rec), rec.shape[0], int(enc_mode), float(pad_value), _p(y))
+    lib().oracle_infer(_p(W), _p(d), len(dims) - 1, _p(rec), rec.shape[0], int(enc_mode), float(pad_value),
+                       int(bool(refl_factor)), _p(y))
     return y
+
+
+def ema(ema_prev, W, t: int, alpha: float = 0.99) -> np.ndarray:
+    """The weight average after step t >= 1 (Eq. 2, bias-corrected reading)."""
+    out = _f64(ema_prev).copy()
+    lib().oracle_ema(_p(out), _p(_f64(W)), out.size, int(t), float(alpha))
+    return out
+
+
+def factor(rec, y) -> np.ndarray:
+    """y (n x 3) times the records' diffuse + specular albedo, per channel."""
+    rec, out = _f32(rec).reshape(-1, 16), _f64(y).copy()
+    lib().oracle_factor(_p(rec), rec.shape[0], _p(out))
+    return out
 
 
 class TrainState:
     """FP64 master weights, Adam moments and step counter of one cache."""
 
-    def __init__(self, W, dims):
+    def __init__(self, W, dims, ema_alpha: float | None = None):
         self.dims = list(dims)
         self.W = _f64(W).copy()
         self.m = np.zeros_like(self.W)
         self.v = np.zeros_like(self.W)
         self.t = 0
+        self.ema_alpha = ema_alpha
+        self.ema = self.W.copy() if ema_alpha is not None else None
 
     def step(self, pool, target, batch: int, frame_seed: int, step: int, enc_mode=ENC_CHEAP, pad_value=1.0,
              loss_mode=LOSS_LUMINANCE, loss_eps=0.01, lr=1e-2, b1=0.9, b2=0.99, adam_eps=1e-8,
-             want_grad: bool = False):
+             refl_factor: bool = False, want_grad: bool = False):
         pool, target = _f32(pool), _f32(target)
         t = ctypes.c_int64(self.t)
         grad = np.zeros_like(self.W) if want_grad else None
         val = lib().oracle_train_step(_p(self.W), _p(self.m), _p(self.v), ctypes.byref(t), _p(_dims(self.dims)),
                                       len(self.dims) - 1, _p(pool), _p(target), pool.shape[0], int(batch),
                                       int(frame_seed), int(step), int(enc_mode), float(pad_value), int(loss_mode),
-                                      float(loss_eps), lr, b1, b2, adam_eps, _p(grad))
+                                      float(loss_eps), lr, b1, b2, adam_eps, int(bool(refl_factor)), _p(grad))
         self.t = t.value
+        if self.ema is not None:
+            lib().oracle_ema(_p(self.ema), _p(self.W), self.W.size, self.t, float(self.ema_alpha))
         return (val, grad) if want_grad else val
