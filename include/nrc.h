@@ -101,6 +101,15 @@ typedef struct nrc_config {
   float adam_eps;        /* Adam epsilon; 1e-8 */
   float loss_eps;        /* epsilon of Eq. 5; 0.01 */
   uint64_t seed;         /* seed of the Xavier-uniform initial weights */
+  int32_t ema;           /* 1: keep the weight average of Sec. 3.3, Eq. 2 (read as the bias-corrected
+                            average EMA_t = ((1-a) W_t + a eta_{t-1} EMA_{t-1}) / eta_t, eta_t = 1 - a^t),
+                            updated by every training step, and query the cache with it; 0 (default):
+                            query with the trained weights */
+  float ema_alpha;       /* a of Eq. 2; 0.99 */
+  int32_t refl_factor;   /* 1: reflectance factorisation (Sec. 5): the prediction is the network output
+                            times the record's diffuse + specular albedo (a + b, per channel), in queries and
+                            in the training loss; 0 (default) */
+  int32_t reserved;      /* must be 0 */
 } nrc_config;
 
 typedef struct nrc_cache nrc_cache;
@@ -394,6 +403,17 @@ NRC_API nrc_status nrc_train_step_noalloc(const nrc_config* cfg, float* weights,
                                           int64_t n_pool, int64_t batch, uint64_t frame_seed,
                                           int32_t step_in_frame, float* loss_out, int32_t* err_out,
                                           nrc_stream stream);
+
+/* Weight average of a cache created with cfg.ema = 1 (Sec. 3.3, Eq. 2): copies
+ * the nrc_param_count FP32 averaged weights (layout of nrc_get_state) to the
+ * host buffer ema (synchronises the stream).  Before the first training step
+ * the average equals the weights; nrc_set_state restarts it at the weights
+ * it sets.  NRC_ERR_UNSUPPORTED for a cache without an average. */
+NRC_API nrc_status nrc_get_ema(nrc_cache* cache, float* ema, nrc_stream stream);
+
+/* Replaces the weight average (host buffer, nrc_param_count floats) and the
+ * 16-bit image the queries read (synchronises the stream). */
+NRC_API nrc_status nrc_set_ema(nrc_cache* cache, const float* ema, nrc_stream stream);
 
 /* Why the last failing call on this thread failed ("" if none). */
 NRC_API const char* nrc_last_error_string(void);

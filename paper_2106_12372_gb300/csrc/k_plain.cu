@@ -52,22 +52,29 @@ __global__ void __launch_bounds__(256) k_plain_dense(const float* __restrict__ X
 }
 
 // Relative L2 loss (Eq. 5): G[r] = dL/dy scaled by 1/(3N); per-CTA loss sums
-// go to the loss slot of the CTA's partial.
+// go to the loss slot of the CTA's partial.  With rec (reflectance
+// factorisation, Sec. 5) the loss sees y times the record's diffuse +
+// specular albedo f, and G is dL/d(y f) times f.
 __global__ void __launch_bounds__(kPR) k_plain_loss(const float* __restrict__ Yh, const float* __restrict__ T,
                                                     float* __restrict__ G, int64_t n, int loss_mode, float eps,
-                                                    float inv3n, float* __restrict__ partials, int n_params) {
+                                                    float inv3n, float* __restrict__ partials, int n_params,
+                                                    const float* __restrict__ rec) {
   __shared__ float red[kPR / 32];
   const int64_t r = int64_t(blockIdx.x) * kPR + threadIdx.x;
   float loss_row = 0.0f;
   if (r < n) {
-    const float* y = Yh + r * 3;
+    float y[3], f[3] = {1.0f, 1.0f, 1.0f};
+    for (int ch = 0; ch < 3; ++ch) {
+      if (rec) f[ch] = rec[r * kRecFloats + 8 + ch] + rec[r * kRecFloats + 11 + ch];
+      y[ch] = Yh[r * 3 + ch] * f[ch];
+    }
     const float lum = 0.2126f * y[0] + 0.7152f * y[1] + 0.0722f * y[2];
     for (int ch = 0; ch < 3; ++ch) {
       const float den = (loss_mode == NRC_LOSS_LUMINANCE ? lum * lum : y[ch] * y[ch]) + eps;
       const float inv = 1.0f / den;
       const float diff = y[ch] - T[r * 3 + ch];
       loss_row = fmaf(diff * diff, inv, loss_row);
-      G[r * 3 + ch] = 2.0f * diff * inv * inv3n;
+      G[r * 3 + ch] = 2.0f * diff * inv * inv3n * f[ch];
     }
   }
   float s = loss_row;
@@ -173,6 +180,13 @@ static cudaError_t ensure_plain(Cache* c, size_t bytes) {
   return e;
 }
 
+// Reflectance factorisation of query outputs: rgb[r] *= diffuse + specular albedo.
+__global__ void __launch_bounds__(kPR) k_plain_factor(const float* __restrict__ rec, int64_t n, float* __restrict__ rgb) {
+  const int64_t r = int64_t(blockIdx.x) * kPR + threadIdx.x;
+  if (r >= n) return;
+  for (int ch = 0; ch < 3; ++ch) rgb[r * 3 + ch] *= rec[r * kRecFloats + 8 + ch] + rec[r * kRecFloats + 11 + ch];
+}
+
 cudaError_t plain_infer(Cache* c, const float* rec, int64_t n, float* rgb, cudaStream_t st) {
   const size_t act = size_t(n) * 64;
   cudaError_t e = ensure_plain(c, act * 2 * 4);
@@ -185,7 +199,7 @@ cudaError_t plain_infer(Cache* c, const float* rec, int64_t n, float* rgb, cudaS
   const unsigned blocks = unsigned((n + kPR - 1) / kPR);
   const NetShape& s = c->net;
   for (int l = 0; l < s.n_mats; ++l) {
-    const float* W = c->w + s.w_off[l];
+    const float* W = query_weights(c) + s.w_off[l];
     if (l + 1 < s.n_mats)
       k_plain_dense<true><<<blocks, 256, 0, st>>>(A, W, B, n, s.dims[l + 1]);
     else
@@ -194,6 +208,10 @@ cudaError_t plain_infer(Cache* c, const float* rec, int64_t n, float* rgb, cudaS
     float* t = A;
     A = B;
     B = t;
+  }
+  if (c->cfg.refl_factor) {
+    k_plain_factor<<<blocks, kPR, 0, st>>>(rec, n, rgb);
+    c->launches += 1;
   }
   return cudaGetLastError();
 }
@@ -232,7 +250,7 @@ cudaError_t plain_train(Cache* c, const float* pool, const float* target, int64_
   }
   const float inv3n = float(1.0 / (3.0 * double(batch)));
   k_plain_loss<<<blocks, kPR, 0, st>>>(Y, tgt, G, batch, c->cfg.loss_mode, c->cfg.loss_eps, inv3n, c->partials,
-                                      s.n_params);
+                                      s.n_params, c->cfg.refl_factor ? rec : nullptr);
   c->launches += 1;
   const float* Dcur = G;
   float* Dnext = D0;

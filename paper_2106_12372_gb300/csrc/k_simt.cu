@@ -135,7 +135,8 @@ __device__ __forceinline__ void stage_weights(float* sw, const float* __restrict
 
 template <int MODE>
 __global__ void __launch_bounds__(128) k_infer_simt(const float* __restrict__ rec, int64_t n, float* __restrict__ rgb,
-                                                    const float* __restrict__ w, const __grid_constant__ NetShape net, float pad) {
+                                                    const float* __restrict__ w, const __grid_constant__ NetShape net, float pad,
+                                                    int factor) {
   extern __shared__ float4 smem_f4[];
   float* sw = reinterpret_cast<float*>(smem_f4);
   stage_weights(sw, w, net.n_params);
@@ -151,6 +152,10 @@ __global__ void __launch_bounds__(128) k_infer_simt(const float* __restrict__ re
     }
     float y[3];
     dense_out(sw + net.w_off[net.n_mats - 1], h, y);
+    if (factor) {  // reflectance factorisation (Sec. 5): times diffuse + specular albedo
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) y[ch] *= r[8 + ch] + r[11 + ch];
+    }
     rgb[row * 3 + 0] = y[0];
     rgb[row * 3 + 1] = y[1];
     rgb[row * 3 + 2] = y[2];
@@ -172,9 +177,11 @@ cudaError_t launch_infer_simt(Cache* c, const float* rec, int64_t n, float* rgb,
   const int64_t cap = int64_t(c->sm_count) * 2;
   const unsigned blocks = unsigned(want < cap ? want : cap);
   if (mode == 0)
-    k_infer_simt<0><<<blocks, 128, smem, st>>>(rec, n, rgb, c->w, c->net, c->cfg.pad_value);
+    k_infer_simt<0><<<blocks, 128, smem, st>>>(rec, n, rgb, query_weights(c), c->net, c->cfg.pad_value,
+                                               c->cfg.refl_factor);
   else
-    k_infer_simt<1><<<blocks, 128, smem, st>>>(rec, n, rgb, c->w, c->net, c->cfg.pad_value);
+    k_infer_simt<1><<<blocks, 128, smem, st>>>(rec, n, rgb, query_weights(c), c->net, c->cfg.pad_value,
+                                               c->cfg.refl_factor);
   return cudaGetLastError();
 }
 
@@ -210,7 +217,8 @@ __global__ void __launch_bounds__(kTrainRows) k_train_simt(const float* __restri
                                                          int64_t n_pool, int64_t batch, uint64_t a, uint64_t c,
                                                          int step, const float* __restrict__ w, const __grid_constant__ NetShape net,
                                                          float pad, int loss_mode, float loss_eps, float inv3n,
-                                                         float* __restrict__ partials, long long* __restrict__ t_ctr) {
+                                                         float* __restrict__ partials, long long* __restrict__ t_ctr,
+                                                         int factor) {
   extern __shared__ float4 smem_f4[];
   float* sw = reinterpret_cast<float*>(smem_f4);
   float* Hs = sw + ((net.n_params + 3) & ~3);       // [n_mats][64][kHStride]
@@ -225,12 +233,17 @@ __global__ void __launch_bounds__(kTrainRows) k_train_simt(const float* __restri
   const bool valid = j < batch;
   float h[64], z[64];
   float tg[3] = {0.f, 0.f, 0.f};
+  float fac[3] = {1.f, 1.f, 1.f};
   if (valid) {
     const uint64_t i = uint64_t(step) * uint64_t(batch) + uint64_t(j);
     const int64_t src = int64_t((a * i + c) % uint64_t(n_pool));
     float r[kRecFloats];
     load_record(pool, src, r);
     encode_record<MODE>(r, pad, h);
+    if (factor) {
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) fac[ch] = r[8 + ch] + r[11 + ch];
+    }
     tg[0] = __ldg(target + src * 3);
     tg[1] = __ldg(target + src * 3 + 1);
     tg[2] = __ldg(target + src * 3 + 2);
@@ -255,7 +268,12 @@ __global__ void __launch_bounds__(kTrainRows) k_train_simt(const float* __restri
   }
   float y[3], g[3], loss_row;
   dense_out(sw + net.w_off[net.n_mats - 1], h, y);
+  // factorisation: the loss sees y * f, the network output the gradient times f
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) y[ch] *= fac[ch];
   relative_l2(y, tg, loss_mode, loss_eps, g, &loss_row);
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) g[ch] *= fac[ch];
   if (!valid) {
     g[0] = g[1] = g[2] = 0.0f;
     loss_row = 0.0f;
@@ -383,11 +401,11 @@ cudaError_t launch_train_simt(Cache* c, const float* pool, const float* target, 
   if (mode == 0)
     k_train_simt<0><<<blocks, kTrainRows, smem, st>>>(pool, target, n_pool, batch, a, cc, step, c->w, c->net,
                                                       c->cfg.pad_value, c->cfg.loss_mode, c->cfg.loss_eps, inv3n,
-                                                      c->partials, c->t);
+                                                      c->partials, c->t, c->cfg.refl_factor);
   else
     k_train_simt<1><<<blocks, kTrainRows, smem, st>>>(pool, target, n_pool, batch, a, cc, step, c->w, c->net,
                                                       c->cfg.pad_value, c->cfg.loss_mode, c->cfg.loss_eps, inv3n,
-                                                      c->partials, c->t);
+                                                      c->partials, c->t, c->cfg.refl_factor);
   *n_partials = blocks;
   return cudaGetLastError();
 }
@@ -420,14 +438,17 @@ __device__ __forceinline__ void adam_block(float* __restrict__ w, float* __restr
                                            const long long* __restrict__ t_ctr, const float* __restrict__ partials,
                                            int n_partials, const NetShape& net, const ImageShape& img,
                                            uint8_t* __restrict__ wimg, float grad_scale, float lr, float b1, float b2,
-                                           float eps, float* __restrict__ loss_out, bool do_loss) {
+                                           float eps, float* __restrict__ loss_out, bool do_loss,
+                                           float* __restrict__ ema, uint8_t* __restrict__ wimg_ema, float alpha) {
   __shared__ float red[kAdamGroups][32];
-  __shared__ float corr[2];
+  __shared__ float corr[4];
   const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {  // bias corrections 1 - beta^t, once per block
     const long long t = *t_ctr;
     corr[0] = 1.0f - pow_int(b1, t);
     corr[1] = 1.0f - pow_int(b2, t);
+    corr[2] = 1.0f - pow_int(alpha, t);      // eta_t of Eq. 2
+    corr[3] = 1.0f - pow_int(alpha, t - 1);  // eta_{t-1}
   }
   const size_t stride = partial_stride(net.n_params);
   const int p = blockIdx.x * 32 + lane;
@@ -469,16 +490,26 @@ __device__ __forceinline__ void adam_block(float* __restrict__ w, float* __restr
   v[p] = vn;
   const float wn = w[p] - lr * (mn / c1) / (sqrtf(vn / c2) + eps);
   w[p] = wn;
+  // the weight average of Eq. 2 (bias-corrected reading); it never feeds back
+  // into training
+  float en = 0.0f;
+  if (ema) {
+    en = ((1.0f - alpha) * wn + alpha * corr[3] * ema[p]) / corr[2];
+    ema[p] = en;
+  }
   if (IMG) {
     int l = 0;
     while (l + 1 < net.n_mats && p >= net.w_off[l + 1]) ++l;
     const int q = p - net.w_off[l];
     const int o = q / net.dims[l], i = q % net.dims[l];
-    uint8_t* dst = wimg + img.off[l] + sw128_offset(o, i);
-    if (IMG == 1)
-      *reinterpret_cast<__half*>(dst) = __float2half_rn(wn);
-    else
-      *reinterpret_cast<__nv_bfloat16*>(dst) = __float2bfloat16_rn(wn);
+    const uint32_t off = img.off[l] + sw128_offset(o, i);
+    if (IMG == 1) {
+      *reinterpret_cast<__half*>(wimg + off) = __float2half_rn(wn);
+      if (ema) *reinterpret_cast<__half*>(wimg_ema + off) = __float2half_rn(en);
+    } else {
+      *reinterpret_cast<__nv_bfloat16*>(wimg + off) = __float2bfloat16_rn(wn);
+      if (ema) *reinterpret_cast<__nv_bfloat16*>(wimg_ema + off) = __float2bfloat16_rn(en);
+    }
   }
 }
 
@@ -489,11 +520,13 @@ __global__ void __launch_bounds__(32 * kAdamGroups) k_adam(float* __restrict__ w
                                                            const __grid_constant__ NetShape net,
                                                            const __grid_constant__ ImageShape img,
                                                            uint8_t* __restrict__ wimg, float grad_scale, float lr,
-                                                           float b1, float b2, float eps, float* __restrict__ loss_out) {
+                                                           float b1, float b2, float eps, float* __restrict__ loss_out,
+                                                           float* __restrict__ ema, uint8_t* __restrict__ wimg_ema,
+                                                           float alpha) {
   pdl_wait();  // the partials and the step counter come from the kernel before
   pdl_launch_dependents();
   adam_block<IMG>(w, m, v, t_ctr, partials, n_partials, net, img, wimg, grad_scale, lr, b1, b2, eps, loss_out,
-                  blockIdx.x == 0);
+                  blockIdx.x == 0, ema, wimg_ema, alpha);
 }
 
 // All caches of a batched step: blockIdx.y selects the cache.
@@ -501,12 +534,12 @@ template <int IMG>
 __global__ void __launch_bounds__(32 * kAdamGroups) k_adam_batched(const AdamJob* __restrict__ jobs,
                                                                    const __grid_constant__ NetShape net,
                                                                    const __grid_constant__ ImageShape img, float lr,
-                                                                   float b1, float b2, float eps) {
+                                                                   float b1, float b2, float eps, float alpha) {
   pdl_wait();
   pdl_launch_dependents();
   const AdamJob J = jobs[blockIdx.y];
   adam_block<IMG>(J.w, J.m, J.v, J.t_ctr, J.partials, J.n_partials, net, img, J.wimg, J.grad_scale, lr, b1, b2, eps,
-                  J.loss_out, blockIdx.x == 0);
+                  J.loss_out, blockIdx.x == 0, J.ema, J.wimg_ema, alpha);
 }
 
 cudaError_t launch_adam(Cache* c, int n_partials, float grad_scale, float* loss_out, cudaStream_t st) {
@@ -526,14 +559,18 @@ cudaError_t launch_adam(Cache* c, int n_partials, float grad_scale, float* loss_
   lc.numAttrs = 1;
   const NetShape& net = c->net;
   const ImageShape& img = c->img;
+  float* ema = k.ema ? c->ema : nullptr;
   if (k.dtype == NRC_FP16)
     return cudaLaunchKernelEx(&lc, k_adam<1>, c->w, c->m, c->v, (const long long*)c->t, (const float*)c->partials,
-                              n_partials, net, img, c->wimg, grad_scale, k.lr, k.beta1, k.beta2, k.adam_eps, loss_out);
+                              n_partials, net, img, c->wimg, grad_scale, k.lr, k.beta1, k.beta2, k.adam_eps, loss_out,
+                              ema, c->wimg_ema, k.ema_alpha);
   if (k.dtype == NRC_BF16)
     return cudaLaunchKernelEx(&lc, k_adam<2>, c->w, c->m, c->v, (const long long*)c->t, (const float*)c->partials,
-                              n_partials, net, img, c->wimg, grad_scale, k.lr, k.beta1, k.beta2, k.adam_eps, loss_out);
+                              n_partials, net, img, c->wimg, grad_scale, k.lr, k.beta1, k.beta2, k.adam_eps, loss_out,
+                              ema, c->wimg_ema, k.ema_alpha);
   return cudaLaunchKernelEx(&lc, k_adam<0>, c->w, c->m, c->v, (const long long*)c->t, (const float*)c->partials,
-                            n_partials, net, img, c->wimg, grad_scale, k.lr, k.beta1, k.beta2, k.adam_eps, loss_out);
+                            n_partials, net, img, c->wimg, grad_scale, k.lr, k.beta1, k.beta2, k.adam_eps, loss_out,
+                            ema, c->wimg_ema, k.ema_alpha);
 }
 
 cudaError_t launch_adam_batched(const Cache* proto, const AdamJob* jobs, int n_jobs, cudaStream_t st) {
@@ -547,9 +584,9 @@ cudaError_t launch_adam_batched(const Cache* proto, const AdamJob* jobs, int n_j
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   lc.attrs = attr;
   lc.numAttrs = 1;
-  if (k.dtype == NRC_FP16) return cudaLaunchKernelEx(&lc, k_adam_batched<1>, jobs, proto->net, proto->img, k.lr, k.beta1, k.beta2, k.adam_eps);
-  if (k.dtype == NRC_BF16) return cudaLaunchKernelEx(&lc, k_adam_batched<2>, jobs, proto->net, proto->img, k.lr, k.beta1, k.beta2, k.adam_eps);
-  return cudaLaunchKernelEx(&lc, k_adam_batched<0>, jobs, proto->net, proto->img, k.lr, k.beta1, k.beta2, k.adam_eps);
+  if (k.dtype == NRC_FP16) return cudaLaunchKernelEx(&lc, k_adam_batched<1>, jobs, proto->net, proto->img, k.lr, k.beta1, k.beta2, k.adam_eps, k.ema_alpha);
+  if (k.dtype == NRC_BF16) return cudaLaunchKernelEx(&lc, k_adam_batched<2>, jobs, proto->net, proto->img, k.lr, k.beta1, k.beta2, k.adam_eps, k.ema_alpha);
+  return cudaLaunchKernelEx(&lc, k_adam_batched<0>, jobs, proto->net, proto->img, k.lr, k.beta1, k.beta2, k.adam_eps, k.ema_alpha);
 }
 
 __global__ void k_step_increment(long long* t) { *t += 1; }
@@ -576,17 +613,19 @@ __global__ void k_build_image(const float* __restrict__ w, const __grid_constant
     *reinterpret_cast<__nv_bfloat16*>(dst) = __float2bfloat16_rn(w[p]);
 }
 
-cudaError_t launch_build_image(Cache* c, cudaStream_t st) {
+cudaError_t launch_build_image_of(const Cache* c, const float* w, uint8_t* img, cudaStream_t st) {
   if (c->cfg.dtype == NRC_FP32) return cudaSuccess;
-  cudaError_t e = cudaMemsetAsync(c->wimg, 0, size_t(c->img.off[c->net.n_mats]), st);
+  cudaError_t e = cudaMemsetAsync(img, 0, size_t(c->img.off[c->net.n_mats]), st);
   if (e != cudaSuccess) return e;
   const int threads = 256;
   const int blocks = (c->net.n_params + threads - 1) / threads;
   if (c->cfg.dtype == NRC_FP16)
-    k_build_image<1><<<blocks, threads, 0, st>>>(c->w, c->net, c->img, c->wimg);
+    k_build_image<1><<<blocks, threads, 0, st>>>(w, c->net, c->img, img);
   else
-    k_build_image<2><<<blocks, threads, 0, st>>>(c->w, c->net, c->img, c->wimg);
+    k_build_image<2><<<blocks, threads, 0, st>>>(w, c->net, c->img, img);
   return cudaGetLastError();
 }
+
+cudaError_t launch_build_image(Cache* c, cudaStream_t st) { return launch_build_image_of(c, c->w, c->wimg, st); }
 
 }  // namespace nrc

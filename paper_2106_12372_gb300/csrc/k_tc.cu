@@ -39,6 +39,7 @@ struct InferParams {
   int n_mats;
   ImageShape img;
   float pad;
+  int factor;  // reflectance factorisation (Sec. 5)
   int* err;
 };
 
@@ -51,6 +52,7 @@ struct BatchInferParams {
   int n_mats;
   ImageShape img;
   float pad;
+  int factor;
   int* err;
 };
 
@@ -75,6 +77,16 @@ __device__ __forceinline__ void encode_to_tmem(const float (&r)[kRecFloats], flo
   tmem_st_wait();
 }
 
+// Sum of a staged record's diffuse and specular albedo (floats 8..10 and
+// 11..13: 16-byte chunks 2 and 3, stored at chunk q ^ rot of the 64-byte row).
+__device__ __forceinline__ void staged_albedo_sum(const uint8_t* row, uint32_t rot, float (&f)[3]) {
+  const float4 c2 = *reinterpret_cast<const float4*>(row + ((2u ^ rot) << 4));
+  const float4 c3 = *reinterpret_cast<const float4*>(row + ((3u ^ rot) << 4));
+  f[0] = c2.x + c2.w;
+  f[1] = c2.y + c3.x;
+  f[2] = c2.z + c3.y;
+}
+
 // The layer chain of one tile in one slot (see the file comment): per layer,
 // the warpgroup's barrier, 4 MMAs issued by one thread, one waiter, and the
 // ReLU + 16-bit epilogue back into the activation columns; the output
@@ -90,7 +102,8 @@ struct SlotTmem {
 
 template <bool BF16>
 __device__ __forceinline__ void tile_layers(const ImageShape& img, int n_mats, const SlotTmem& st, uint32_t sw_base,
-                                            int slot, int rit, uint64_t* bar, uint32_t& phase, int* err, float* out) {
+                                            int slot, int rit, uint64_t* bar, uint32_t& phase, int* err, float* out,
+                                            const uint8_t* fac_row, uint32_t rot) {
   for (int l = 0; l < n_mats; ++l) {
     fence_before();
     named_sync(1 + slot, 128);
@@ -123,9 +136,17 @@ __device__ __forceinline__ void tile_layers(const ImageShape& img, int n_mats, c
       uint32_t v[4];
       tmem_ld4(st.t_acc, v);
       if (out) {
-        out[0] = __uint_as_float(v[0]);
-        out[1] = __uint_as_float(v[1]);
-        out[2] = __uint_as_float(v[2]);
+        float y0 = __uint_as_float(v[0]), y1 = __uint_as_float(v[1]), y2 = __uint_as_float(v[2]);
+        if (fac_row) {  // reflectance factorisation: times the record's diffuse + specular albedo
+          float f[3];
+          staged_albedo_sum(fac_row, rot, f);
+          y0 *= f[0];
+          y1 *= f[1];
+          y2 *= f[2];
+        }
+        out[0] = y0;
+        out[1] = y1;
+        out[2] = y2;
       }
     }
   }
@@ -218,10 +239,13 @@ __global__ void __launch_bounds__(kInferThreads, 1) k_infer_tc(const __grid_cons
     cp_async_wait<1>();  // this tile's record has landed (only this thread reads it)
     float r[kRecFloats];
     rs.read(buf, r);
+    // the staged record stays in place until the next tile's prefetch, so the
+    // output epilogue can read its albedos again there
+    const uint8_t* fac_row = p.factor ? rs.p + buf * 8192 : nullptr;
     buf ^= 1;
     encode_to_tmem<MODE, BF16>(r, p.pad, st.t_act);
     tile_layers<BF16>(p.img, p.n_mats, st, sw_base, slot, rit, &bar_mma[slot], phase, p.err,
-                      row < p.n ? p.rgb + row * 3 : nullptr);
+                      row < p.n ? p.rgb + row * 3 : nullptr, fac_row, rs.rot);
   }
   cp_async_wait<0>();
   fence_before();
@@ -308,10 +332,11 @@ __global__ void __launch_bounds__(kInferThreads, 1) k_infer_batched(const __grid
       cp_async_wait<1>();
       float r[kRecFloats];
       rs.read(buf, r);
+      const uint8_t* fac_row = p.factor ? rs.p + buf * 8192 : nullptr;
       buf ^= 1;
       encode_to_tmem<MODE, BF16>(r, p.pad, st.t_act);
       tile_layers<BF16>(p.img, p.n_mats, st, sw_base, slot, rit, &bar_mma[slot], phase, p.err,
-                        row < C.n ? C.rgb + row * 3 : nullptr);
+                        row < C.n ? C.rgb + row * 3 : nullptr, fac_row, rs.rot);
     }
     cp_async_wait<0>();
   }
@@ -339,11 +364,12 @@ cudaError_t launch_infer_tc(Cache* c, const float* rec, int64_t n, float* rgb, c
   p.rec = rec;
   p.n = n;
   p.rgb = rgb;
-  p.wimg = c->wimg;
+  p.wimg = query_image(c);
   p.img_bytes = c->img.off[c->net.n_mats];
   p.n_mats = c->net.n_mats;
   p.img = c->img;
   p.pad = c->cfg.pad_value;
+  p.factor = c->cfg.refl_factor;
   p.err = c->err;
   const int smem = ((p.img_bytes + 1023) & ~1023) + kSlots * 2 * 8192 + 1024;
   const int64_t n_tiles = (n + kTile - 1) / kTile;
@@ -381,6 +407,7 @@ cudaError_t launch_infer_batched(const Cache* proto, const BatchCache* caches, c
   p.n_mats = proto->net.n_mats;
   p.img = proto->img;
   p.pad = proto->cfg.pad_value;
+  p.factor = proto->cfg.refl_factor;
   p.err = proto->err;
   const int smem = ((p.img_bytes + 1023) & ~1023) + kSlots * 2 * 8192 + 1024;
   const bool bf16 = proto->cfg.dtype == NRC_BF16;
@@ -444,6 +471,7 @@ struct TrainParams {
   float pad;
   int loss_mode;
   float loss_eps;
+  int factor;  // reflectance factorisation (Sec. 5)
   float inv3n;
   float* partials;
   long long* t_ctr;
@@ -605,11 +633,15 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(const __grid_cons
   for (int64_t tile = J.tile_begin; tile < J.tile_end; tile += J.tile_step) {
     const int64_t j = tile * kTile + r;
     const bool valid = j < J.batch;
-    float rec[kRecFloats], tg[3] = {0.f, 0.f, 0.f};
+    float rec[kRecFloats], tg[3] = {0.f, 0.f, 0.f}, fac[3] = {1.f, 1.f, 1.f};
     if (valid) {
       const uint64_t i = uint64_t(J.step) * uint64_t(J.batch) + uint64_t(j);
       const int64_t src = int64_t((J.a * i + J.c) % uint64_t(J.n_pool));
       load_record(J.pool, src, rec);
+      if (p.factor) {
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) fac[ch] = rec[8 + ch] + rec[11 + ch];
+      }
       if (half == 0) {
         tg[0] = __ldg(J.target + src * 3);
         tg[1] = __ldg(J.target + src * 3 + 1);
@@ -676,6 +708,9 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(const __grid_cons
 #pragma unroll
     for (int q = 0; q < 16; ++q) pk[q] = 0u;
     if (half == 0) {
+      // factorisation: the loss sees y * f; the gradient reaching the network is times f
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) y[ch] *= fac[ch];
       const float lum = 0.2126f * y[0] + 0.7152f * y[1] + 0.0722f * y[2];
       float lr = 0.0f, g[3];
 #pragma unroll
@@ -684,7 +719,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(const __grid_cons
         const float inv = 1.0f / den;
         const float diff = y[ch] - tg[ch];
         lr = fmaf(diff * diff, inv, lr);
-        g[ch] = valid ? fminf(fmaxf(2.0f * diff * inv, -60000.0f), 60000.0f) : 0.0f;
+        g[ch] = valid ? fminf(fmaxf(2.0f * diff * inv * fac[ch], -60000.0f), 60000.0f) : 0.0f;
       }
       loss_acc += valid ? lr : 0.0f;
       pk[0] = pack2<BF16, false>(g[0], g[1]);
@@ -793,6 +828,7 @@ cudaError_t launch_train_tc(Cache* c, const float* pool, const float* target, in
   p.pad = c->cfg.pad_value;
   p.loss_mode = c->cfg.loss_mode;
   p.loss_eps = c->cfg.loss_eps;
+  p.factor = c->cfg.refl_factor;
   p.inv3n = float(1.0 / (3.0 * double(batch)));
   p.t_ctr = c->t;
   p.wimg = c->wimg;
@@ -852,6 +888,7 @@ cudaError_t launch_train_batched(const Cache* proto, const TrainJob* jobs, int n
   p.pad = proto->cfg.pad_value;
   p.loss_mode = proto->cfg.loss_mode;
   p.loss_eps = proto->cfg.loss_eps;
+  p.factor = proto->cfg.refl_factor;
   p.err = proto->err;
   const int smem = ((p.img_bytes + 1023) & ~1023) + p.n_mats * 16384 + 2 * 16384 + 1024;
   const bool bf16 = proto->cfg.dtype == NRC_BF16;

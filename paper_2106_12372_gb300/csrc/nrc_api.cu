@@ -124,6 +124,10 @@ static nrc_status check_cfg(const nrc_config* cfg) {
   if (!(cfg->lr > 0.0f) || !(cfg->beta1 >= 0.0f && cfg->beta1 < 1.0f) || !(cfg->beta2 >= 0.0f && cfg->beta2 < 1.0f) ||
       !(cfg->adam_eps >= 0.0f) || !(cfg->loss_eps > 0.0f) || !std::isfinite(cfg->pad_value))
     return set_error("invalid optimiser or loss constants"), NRC_ERR_INVALID_ARG;
+  if ((cfg->ema != 0 && cfg->ema != 1) || (cfg->ema && !(cfg->ema_alpha >= 0.0f && cfg->ema_alpha < 1.0f)))
+    return set_error("ema must be 0 or 1 and ema_alpha in [0, 1)"), NRC_ERR_INVALID_ARG;
+  if ((cfg->refl_factor != 0 && cfg->refl_factor != 1) || cfg->reserved != 0)
+    return set_error("refl_factor must be 0 or 1 and reserved 0"), NRC_ERR_INVALID_ARG;
   return NRC_OK;
 }
 
@@ -168,7 +172,24 @@ void nrc_default_config(nrc_config* cfg) {
   cfg->adam_eps = 1e-8f;
   cfg->loss_eps = 0.01f;
   cfg->seed = 2106;
+  cfg->ema = 0;
+  cfg->ema_alpha = 0.99f;
+  cfg->refl_factor = 0;
+  cfg->reserved = 0;
 }
+
+namespace nrc {
+// Restarts the weight average at the current weights (cache creation,
+// nrc_set_state): EMA_0 is never read by Eq. 2 (eta_0 = 0), but queries made
+// before the first training step see it.
+static cudaError_t reset_ema(Cache* c, cudaStream_t st) {
+  if (!c->cfg.ema) return cudaSuccess;
+  cudaError_t e = cudaMemcpyAsync(c->ema, c->w, size_t(c->net.n_params) * 4, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess && c->cfg.dtype != NRC_FP32)
+    e = cudaMemcpyAsync(c->wimg_ema, c->wimg, size_t(c->img.off[c->net.n_mats]), cudaMemcpyDeviceToDevice, st);
+  return e;
+}
+}  // namespace nrc
 
 int64_t nrc_param_count(const nrc_cache* c) { return c ? c->net.n_params : 0; }
 
@@ -180,6 +201,8 @@ static void free_cache(nrc_cache* c) {
   cudaFree(c->v);
   cudaFree(c->t);
   cudaFree(c->wimg);
+  cudaFree(c->ema);
+  cudaFree(c->wimg_ema);
   cudaFree(c->partials);
   cudaFree(c->err);
   cudaFree(c->plain_buf);
@@ -216,6 +239,8 @@ nrc_status nrc_create(const nrc_config* cfg, nrc_stream stream, nrc_cache** out)
   if (e == cudaSuccess) e = cudaMalloc(&c->t, sizeof(long long));
   if (e == cudaSuccess) e = cudaMalloc(&c->wimg, size_t(c->img.off[c->net.n_mats]) + 1024);
   if (e == cudaSuccess) e = cudaMalloc(&c->err, sizeof(int));
+  if (e == cudaSuccess && cfg->ema) e = cudaMalloc(&c->ema, np * 4);
+  if (e == cudaSuccess && cfg->ema) e = cudaMalloc(&c->wimg_ema, size_t(c->img.off[c->net.n_mats]) + 1024);
   if (e != cudaSuccess) {
     nrc_status st = cuda_status(e, "nrc_create allocation");
     free_cache(c);
@@ -231,6 +256,7 @@ nrc_status nrc_create(const nrc_config* cfg, nrc_stream stream, nrc_cache** out)
   if (e == cudaSuccess) e = cudaMemsetAsync(c->err, 0, sizeof(int), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->wimg, 0, size_t(c->img.off[c->net.n_mats]) + 1024, st);
   if (e == cudaSuccess) e = launch_build_image(c, st);
+  if (e == cudaSuccess) e = reset_ema(c, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // w0 is a host temporary
   if (e != cudaSuccess) {
     nrc_status s2 = cuda_status(e, "nrc_create upload");
@@ -431,8 +457,28 @@ nrc_status nrc_set_state(nrc_cache* c, const float* w, const float* m, const flo
   if (e == cudaSuccess) e = v ? cudaMemcpyAsync(c->v, v, bytes, cudaMemcpyHostToDevice, st) : cudaMemsetAsync(c->v, 0, bytes, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->t, &t, sizeof(t), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = launch_build_image(c, st);
+  if (e == cudaSuccess) e = reset_ema(c, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   return cuda_status(e, "nrc_set_state");
+}
+
+nrc_status nrc_get_ema(nrc_cache* c, float* ema, nrc_stream stream) {
+  if (!c || !ema) return set_error("cache or output NULL"), NRC_ERR_INVALID_ARG;
+  if (!c->cfg.ema) return set_error("the cache keeps no weight average (cfg.ema = 0)"), NRC_ERR_UNSUPPORTED;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(ema, c->ema, size_t(c->net.n_params) * 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return cuda_status(e, "nrc_get_ema");
+}
+
+nrc_status nrc_set_ema(nrc_cache* c, const float* ema, nrc_stream stream) {
+  if (!c || !ema) return set_error("cache or input NULL"), NRC_ERR_INVALID_ARG;
+  if (!c->cfg.ema) return set_error("the cache keeps no weight average (cfg.ema = 0)"), NRC_ERR_UNSUPPORTED;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(c->ema, ema, size_t(c->net.n_params) * 4, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && c->cfg.dtype != NRC_FP32) e = launch_build_image_of(c, c->ema, c->wimg_ema, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return cuda_status(e, "nrc_set_ema");
 }
 
 nrc_status nrc_check_error(nrc_cache* c, nrc_stream stream) {

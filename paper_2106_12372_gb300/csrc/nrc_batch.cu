@@ -25,7 +25,8 @@ static uint8_t* ring_slot(Batch* b, int* idx) {
 bool batch_same_cfg(const nrc_config& a, const nrc_config& b) {
   return a.width == b.width && a.hidden_layers == b.hidden_layers && a.dtype == b.dtype && a.enc_mode == b.enc_mode &&
          a.loss_mode == b.loss_mode && a.pad_value == b.pad_value && a.lr == b.lr && a.beta1 == b.beta1 &&
-         a.beta2 == b.beta2 && a.adam_eps == b.adam_eps && a.loss_eps == b.loss_eps;
+         a.beta2 == b.beta2 && a.adam_eps == b.adam_eps && a.loss_eps == b.loss_eps && a.ema == b.ema &&
+         (!a.ema || a.ema_alpha == b.ema_alpha) && a.refl_factor == b.refl_factor;
 }
 
 nrc_status batch_check(nrc_cache* const* caches, int n_caches) {
@@ -125,7 +126,7 @@ nrc_status batch_infer(Batch* b, nrc_cache* const* caches, int nc, const float* 
     if (n[c] > 0 && (!records[c] || !rgb[c] || (reinterpret_cast<uintptr_t>(records[c]) & 15u)))
       return set_error("batched query: buffers of cache %d NULL or misaligned", c), NRC_ERR_INVALID_ARG;
     if (n[c] > (int64_t(1) << 38)) return set_error("batched query: n[%d] too large", c), NRC_ERR_INVALID_ARG;
-    hc[c] = BatchCache{caches[c]->wimg, records[c], rgb[c], n[c]};
+    hc[c] = BatchCache{query_image(caches[c]), records[c], rgb[c], n[c]};
     const int64_t tiles = (n[c] + kTile - 1) / kTile;
     for (int64_t t = 0; t < tiles; t += b->unit_tiles)
       hu.push_back(BatchUnit{c, int(t), int(std::min<int64_t>(tiles, t + b->unit_tiles))});
@@ -227,7 +228,8 @@ nrc_status batch_train_step(Batch* b, nrc_cache* const* caches, int nc, const fl
       J.bump_t = q == 0;
       J.inv3n = float(1.0 / (3.0 * double(batch[c])));
     }
-    ha[n_adam++] = AdamJob{cc->w, cc->m, cc->v, cc->t, b->d_partials + size_t(j0) * b->stride, k[c], cc->wimg,
+    ha[n_adam++] = AdamJob{cc->w, cc->m, cc->v, cc->cfg.ema ? cc->ema : nullptr, cc->wimg_ema, cc->t,
+                           b->d_partials + size_t(j0) * b->stride, k[c], cc->wimg,
                            float(1.0 / (3.0 * double(batch[c]))), loss_out ? loss_out[c] : nullptr};
   }
   cudaError_t e = cudaMemcpyAsync(b->d_jobs, hj, sizeof(TrainJob) * j, cudaMemcpyHostToDevice, st);

@@ -57,6 +57,8 @@ struct Cache {
   float* v = nullptr;     // Adam second moment
   long long* t = nullptr; // Adam step counter (device)
   uint8_t* wimg = nullptr;        // 16-bit weight image (tensor-core path)
+  float* ema = nullptr;           // weight average of Eq. 2 (cfg.ema), FP32 [n_params]
+  uint8_t* wimg_ema = nullptr;    // its 16-bit image (what queries read when cfg.ema)
   float* partials = nullptr;      // [max_partials][partial_stride] weight-gradient partials; loss at [n_params]
   int max_partials = 0;
   int* err = nullptr;     // device error word
@@ -107,6 +109,8 @@ struct AdamJob {
   float* w;
   float* m;
   float* v;
+  float* ema;          // null: no weight average
+  uint8_t* wimg_ema;
   const long long* t_ctr;
   const float* partials;
   int n_partials;
@@ -138,6 +142,11 @@ cudaError_t launch_train_simt(Cache* c, const float* pool, const float* target, 
                               uint64_t a, uint64_t cc, int step, int* n_partials, cudaStream_t st);
 cudaError_t launch_adam(Cache* c, int n_partials, float grad_scale, float* loss_out, cudaStream_t st);
 cudaError_t launch_build_image(Cache* c, cudaStream_t st);
+// 16-bit image of an arbitrary FP32 weight set of c's shape into img.
+cudaError_t launch_build_image_of(const Cache* c, const float* w, uint8_t* img, cudaStream_t st);
+// What queries read: the weight average when the cache keeps one.
+inline const float* query_weights(const Cache* c) { return c->cfg.ema ? c->ema : c->w; }
+inline const uint8_t* query_image(const Cache* c) { return c->cfg.ema ? c->wimg_ema : c->wimg; }
 cudaError_t launch_step_increment(Cache* c, cudaStream_t st);
 cudaError_t launch_infer_tc(Cache* c, const float* rec, int64_t n, float* rgb, cudaStream_t st);
 // One persistent launch over the units of several caches (device arrays);

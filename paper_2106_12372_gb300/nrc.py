@@ -50,6 +50,10 @@ class Config(ctypes.Structure):
         ("adam_eps", ctypes.c_float),
         ("loss_eps", ctypes.c_float),
         ("seed", ctypes.c_uint64),
+        ("ema", ctypes.c_int32),
+        ("ema_alpha", ctypes.c_float),
+        ("refl_factor", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -134,6 +138,8 @@ def lib() -> ctypes.CDLL:
             "nrc_batch_set_unit_tiles": (i32, [P, i32]),
             "nrc_batch_autotune": (i32, [P, P, P, P, P, P]),
             "nrc_batch_set_train_tiles": (i32, [P, i32]),
+            "nrc_get_ema": (i32, [P, P, P]),
+            "nrc_set_ema": (i32, [P, P, P]),
             "nrc_server_default_config": (None, [P]),
             "nrc_now_ns": (i64, []),
             "nrc_server_create": (i32, [P, P, P]),
@@ -291,6 +297,16 @@ class Cache:
         v = None if v is None else np.ascontiguousarray(v, dtype=np.float32)
         _check(lib().nrc_set_state(self._h, w.ctypes.data, None if m is None else m.ctypes.data,
                                    None if v is None else v.ctypes.data, step, _stream(stream)))
+
+    def get_ema(self, stream=None):
+        """The weight average (cfg.ema = 1) as an FP32 host array."""
+        out = np.zeros(self.n_params, dtype=np.float32)
+        _check(lib().nrc_get_ema(self._h, out.ctypes.data, _stream(stream)))
+        return out
+
+    def set_ema(self, ema, stream=None) -> None:
+        a = np.ascontiguousarray(ema, dtype=np.float32)
+        _check(lib().nrc_set_ema(self._h, a.ctypes.data, _stream(stream)))
 
     def check_error(self, stream=None) -> None:
         _check(lib().nrc_check_error(self._h, _stream(stream)))
