@@ -44,7 +44,7 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle samples every 50 ms while running."""
+    """nvidia-smi clock / throttle samples every 20 ms while running."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -57,7 +57,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -83,6 +83,27 @@ class ClockSampler:
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip().lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(rows)}
+
+
+def infer_traffic():
+    """DRAM bytes per k_infer_tc launch from the committed ncu summary, or None
+    once the kernel's sources differ from the ones that were profiled."""
+    import hashlib
+    import re
+
+    prof = os.path.join(ROOT, "profiles", "k_infer_tc_1080p_fp16.md")
+    if not os.path.exists(prof):
+        return None
+    text = open(prof).read()
+    mt = re.search(r"^traffic_bytes_per_launch: (\d+)", text, re.M)
+    mh = re.search(r"^source_sha256_16: ([0-9a-f]{16})", text, re.M)
+    if not (mt and mh):
+        return None
+    csrc = os.path.join(ROOT, "paper_2106_12372_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in ("k_tc.cu", "tc_ptx.cuh", "nrc_internal.cuh"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return int(mt.group(1)) if h.hexdigest()[:16] == mh.group(1) else None
 
 
 def dist_env():
@@ -454,7 +475,7 @@ def run_gpu(args):
         "batched_caches": batched,
         "serving": serving,
         "roofline": {"kernel": "k_infer_tc (fused encode + 6 tcgen05 layers)", "bound": "tensor", "achieved": achieved,
-                     "peak": burst, "unit": "TFLOP/s", "frac": achieved / burst, "traffic": None,
+                     "peak": burst, "unit": "TFLOP/s", "frac": achieved / burst, "traffic": infer_traffic(),
                      "peak_source": f"{src} bf16 dense burst (fp16 peak = bf16 peak)"},
         "cpu_baseline": cpu,
         "e2e": {"value": N_QUERIES / e2e_s / 1e6, "unit": "Mqueries/s", "h2d_bytes_per_step": h2d,
@@ -469,7 +490,7 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="nrc", choices=["nrc", "reference"])
     ap.add_argument("--dtype", default="fp16", choices=["fp16", "bf16", "fp32"])

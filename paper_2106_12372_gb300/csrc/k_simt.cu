@@ -443,13 +443,6 @@ __device__ __forceinline__ void adam_block(float* __restrict__ w, float* __restr
   __shared__ float red[kAdamGroups][32];
   __shared__ float corr[4];
   const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
-  if (threadIdx.x == 0) {  // bias corrections 1 - beta^t, once per block
-    const long long t = *t_ctr;
-    corr[0] = 1.0f - pow_int(b1, t);
-    corr[1] = 1.0f - pow_int(b2, t);
-    corr[2] = 1.0f - pow_int(alpha, t);      // eta_t of Eq. 2
-    corr[3] = 1.0f - pow_int(alpha, t - 1);  // eta_{t-1}
-  }
   const size_t stride = partial_stride(net.n_params);
   const int p = blockIdx.x * 32 + lane;
   if (do_loss && grp == 1 && loss_out) {
@@ -475,6 +468,15 @@ __device__ __forceinline__ void adam_block(float* __restrict__ w, float* __restr
     }
     for (; k < n_partials; k += kAdamGroups) a[0] += __ldcg(src + size_t(k) * stride);
     part = (a[0] + a[1]) + (a[2] + a[3]);
+  }
+  if (threadIdx.x == 0) {  // bias corrections, once per block (after this thread's loads are in flight)
+    const long long t = *t_ctr;
+    corr[0] = 1.0f - pow_int(b1, t);
+    corr[1] = 1.0f - pow_int(b2, t);
+    if (ema) {
+      corr[2] = 1.0f - pow_int(alpha, t);      // eta_t of Eq. 2
+      corr[3] = 1.0f - pow_int(alpha, t - 1);  // eta_{t-1}
+    }
   }
   red[grp][lane] = part;
   __syncthreads();
