@@ -223,3 +223,86 @@ class TrainState:
         if self.ema is not None:
             lib().oracle_ema(_p(self.ema), _p(self.W), self.W.size, self.t, float(self.ema_alpha))
         return (val, grad) if want_grad else val
+
+
+# ----------------------------------------------------------------- Shampoo --
+# The second-order optimiser the paper evaluated against Adam (Sec. 5,
+# "Optimizer": Shampoo, Gupta et al. 2018, with the refinements of Anil et al.
+# 2020).  The paper gives no constants; the reading implemented here:
+#   per weight matrix W_l (out x in) with gradient G_l,
+#     m   <- b1 m + (1 - b1) G                      (momentum, as Adam's)
+#     v   <- b2 v + (1 - b2) G*G                    (Adam's second moment, for grafting)
+#     L_l <- b2 L_l + (1 - b2) G G^T,  R_l <- b2 R_l + (1 - b2) G^T G
+#     every `interval` steps (from step 1):
+#       P_L = (L_l / (1 - b2^t) + eps_l I)^(-1/4),  eps_l = eps_rel * tr(.)/n, same for R
+#     D   = P_L  m^  P_R,   m^ = m / (1 - b1^t)
+#     A   = m^ / (sqrt(v / (1 - b2^t)) + adam_eps)  (Adam's step)
+#     W_l <- W_l - lr * D * ||A||_F / ||D||_F        (layer-wise grafting of Adam's step size)
+# For 1x1 matrices the step is exactly Adam's.  Inverse roots by a symmetric
+# eigendecomposition in FP64 (numpy.linalg.eigh).
+
+
+def inverse_root(A: np.ndarray, p: int = 4) -> np.ndarray:
+    """A^(-1/p) of a symmetric positive definite matrix (FP64 eigendecomposition)."""
+    w, V = np.linalg.eigh(np.asarray(A, dtype=np.float64))
+    return (V * w ** (-1.0 / p)) @ V.T
+
+
+def shampoo_update(W, m, v, Ls, Rs, Ps, G, t: int, dims, lr=1e-2, b1=0.9, b2=0.99, adam_eps=1e-8,
+                   eps_rel=1e-4, interval: int = 4):
+    """One Shampoo step (t >= 1) on flat FP64 arrays W, m, v and per-layer lists
+    Ls, Rs (statistics) and Ps (list of [P_L, P_R] or None); updated in place."""
+    off = 0
+    recompute = (t - 1) % interval == 0
+    m *= b1
+    m += (1.0 - b1) * G
+    v *= b2
+    v += (1.0 - b2) * G * G
+    for l in range(len(dims) - 1):
+        n_out, n_in = dims[l + 1], dims[l]
+        sl = slice(off, off + n_out * n_in)
+        off += n_out * n_in
+        Gl = G[sl].reshape(n_out, n_in)
+        Ls[l] *= b2
+        Ls[l] += (1.0 - b2) * Gl @ Gl.T
+        Rs[l] *= b2
+        Rs[l] += (1.0 - b2) * Gl.T @ Gl
+        if recompute or Ps[l] is None:
+            roots = []
+            for S in (Ls[l], Rs[l]):
+                Sh = S / (1.0 - b2 ** t)
+                n = Sh.shape[0]
+                roots.append(inverse_root(Sh + (eps_rel * np.trace(Sh) / n + 1e-30) * np.eye(n)))
+            Ps[l] = roots
+        mh = m[sl].reshape(n_out, n_in) / (1.0 - b1 ** t)
+        D = Ps[l][0] @ mh @ Ps[l][1]
+        A = mh / (np.sqrt(v[sl].reshape(n_out, n_in) / (1.0 - b2 ** t)) + adam_eps)
+        nd = np.linalg.norm(D)
+        W[sl] -= lr * (D * (np.linalg.norm(A) / nd if nd > 0 else 0.0)).ravel()
+
+
+class ShampooState:
+    """FP64 weights and Shampoo state of one cache (training step as TrainState.step)."""
+
+    def __init__(self, W, dims, lr=1e-2, eps_rel=1e-4, interval: int = 4):
+        self.dims = list(dims)
+        self.W = _f64(W).copy()
+        self.m = np.zeros_like(self.W)
+        self.v = np.zeros_like(self.W)
+        self.Ls = [np.zeros((dims[l + 1], dims[l + 1])) for l in range(len(dims) - 1)]
+        self.Rs = [np.zeros((dims[l], dims[l])) for l in range(len(dims) - 1)]
+        self.Ps = [None] * (len(dims) - 1)
+        self.t = 0
+        self.lr, self.eps_rel, self.interval = lr, eps_rel, interval
+
+    def step(self, pool, target, batch: int, frame_seed: int, step: int, enc_mode=ENC_CHEAP, pad_value=1.0,
+             loss_mode=LOSS_LUMINANCE, loss_eps=0.01, want_grad: bool = False):
+        rec, tgt, _ = gather(pool, target, batch, frame_seed, step)
+        x = encode(rec, enc_mode, pad_value)
+        y, acts = forward(self.W, self.dims, x, keep_acts=True)
+        val, g = loss(y, tgt, loss_mode, loss_eps)
+        G = backward(self.W, self.dims, acts, g)
+        self.t += 1
+        shampoo_update(self.W, self.m, self.v, self.Ls, self.Rs, self.Ps, G, self.t, self.dims, lr=self.lr,
+                       eps_rel=self.eps_rel, interval=self.interval)
+        return (val, G) if want_grad else val
