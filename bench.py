@@ -272,6 +272,34 @@ def run_batched(queries, dtype: str, frames: int, flush):
     }
 
 
+def run_shampoo(pool, tgt, dtype: str, frames: int, flush):
+    """The frame's 4 training steps with Shampoo (roots once per frame) against
+    Adam on the same pool: milliseconds per frame of training."""
+    import numpy as np
+    import torch
+
+    from paper_2106_12372_gb300 import nrc, synth
+
+    out = {}
+    st = torch.cuda.current_stream()
+    for name, opt in (("adam", nrc.OPT_ADAM), ("shampoo", nrc.OPT_SHAMPOO)):
+        c = nrc.Cache(dtype=dtype, optimizer=opt, seed=2106)
+        for f in range(3):
+            c.frame(pool[:0], pool[:0], pool, tgt, BATCH, N_STEPS, synth.frame_seed(2106, f))
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(frames)]
+        for f in range(frames):
+            flush.zero_()
+            ev[f][0].record(st)
+            c.frame(pool[:0], pool[:0], pool, tgt, BATCH, N_STEPS, synth.frame_seed(2106, 3 + f))
+            ev[f][1].record(st)
+        torch.cuda.synchronize()
+        c.check_error()
+        out[name + "_train_ms_per_frame"] = float(np.median([e[0].elapsed_time(e[1]) for e in ev]))
+        c.close()
+    out["workload"] = "4 training steps x 16,384 records per frame; Shampoo roots recomputed once per frame"
+    return out
+
+
 def run_serving(queries, dtype: str, seconds: float):
     """Eight viewports (4 x 1920x1080, 4 x 3840x2160) with Poisson frame
     arrivals at 30-120 Hz each (rates seeded), served by the continuous-
@@ -428,10 +456,11 @@ def run_gpu(args):
             plain_ms.append(pev[0].elapsed_time(pev[1]))
     plain.close()
 
-    batched = serving = None
+    batched = serving = shampoo = None
     if not args.no_extras and ws == 1 and args.dtype != "fp32":
         batched = run_batched(queries, args.dtype, 30, flush)
         serving = run_serving(queries, args.dtype, args.serve_seconds)
+        shampoo = run_shampoo(pool, tgt, args.dtype, 30, flush)
 
     # end to end: host (pinned) buffers through nrc_frame_host, copies inside the timed region
     qh = torch.from_numpy(synth.make_records(N_QUERIES, seed=seed + 7)).pin_memory()
@@ -474,6 +503,7 @@ def run_gpu(args):
         "plain_fp32_ms_per_frame": statistics.median(plain_ms) if plain_ms else None,
         "batched_caches": batched,
         "serving": serving,
+        "shampoo": shampoo,
         "roofline": {"kernel": "k_infer_tc (fused encode + 6 tcgen05 layers)", "bound": "tensor", "achieved": achieved,
                      "peak": burst, "unit": "TFLOP/s", "frac": achieved / burst, "traffic": infer_traffic(),
                      "peak_source": f"{src} bf16 dense burst (fp16 peak = bf16 peak)"},

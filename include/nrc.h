@@ -88,6 +88,11 @@ enum { NRC_LOSS_LUMINANCE = 0, NRC_LOSS_PER_CHANNEL = 1 };
  * with every activation round-tripping through HBM (a reference point). */
 enum { NRC_PATH_FUSED = 0, NRC_PATH_PLAIN = 1 };
 
+enum {
+  NRC_OPT_ADAM = 0,
+  NRC_OPT_SHAMPOO = 1
+};
+
 typedef struct nrc_config {
   int32_t width;         /* hidden width; 64 */
   int32_t hidden_layers; /* number of hidden layers; 5 (1..8) */
@@ -109,7 +114,12 @@ typedef struct nrc_config {
   int32_t refl_factor;   /* 1: reflectance factorisation (Sec. 5): the prediction is the network output
                             times the record's diffuse + specular albedo (a + b, per channel), in queries and
                             in the training loss; 0 (default) */
-  int32_t reserved;      /* must be 0 */
+  int32_t optimizer;     /* NRC_OPT_ADAM (default; Sec. 5) | NRC_OPT_SHAMPOO (the second-order variant
+                            Sec. 5 reports; read as Gupta et al. 2018 with the exponential statistics, root
+                            interval and Adam grafting of Anil et al. 2020: per weight matrix
+                            W -= lr * D ||A|| / ||D||, D = L^-1/4 m^ R^-1/4, A = Adam's step) */
+  int32_t shampoo_interval; /* steps between inverse-root updates; 4 (once per frame) */
+  float shampoo_eps;     /* relative regulariser eps * tr(S)/n added to each statistic; 1e-4 */
 } nrc_config;
 
 typedef struct nrc_cache nrc_cache;

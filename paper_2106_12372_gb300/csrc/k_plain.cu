@@ -269,7 +269,8 @@ cudaError_t plain_train(Cache* c, const float* pool, const float* target, int64_
   // t is incremented by a one-element add so that Adam sees this step's t.
   e = launch_step_increment(c, st);
   if (e != cudaSuccess) return e;
-  e = launch_adam(c, int(blocks), 1.0f, loss_out, st);
+  e = c->cfg.optimizer == NRC_OPT_SHAMPOO ? launch_shampoo(c, int(blocks), 1.0f, loss_out, st)
+                                          : launch_adam(c, int(blocks), 1.0f, loss_out, st);
   c->launches += 2;
   return e;
 }

@@ -420,18 +420,6 @@ cudaError_t launch_train_simt(Cache* c, const float* pool, const float* target, 
 // warp order.  Block 0's warp 1 also sums the loss slots.
 constexpr int kAdamGroups = 8;
 
-// b^t for integer t >= 0 by repeated squaring in FP32: exact for t = 1, about
-// 2 log2(t) roundings otherwise (FP64 arithmetic is slow on this part).
-__device__ __forceinline__ float pow_int(float b, long long t) {
-  float r = 1.0f;
-  while (t > 0) {
-    if (t & 1) r *= b;
-    b *= b;
-    t >>= 1;
-  }
-  return r;
-}
-
 // One block: the 32 weights p = blockIdx.x * 32 + lane of one cache.
 template <int IMG>  // 0: no image, 1: FP16, 2: BF16
 __device__ __forceinline__ void adam_block(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,

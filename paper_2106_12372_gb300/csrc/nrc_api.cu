@@ -126,8 +126,11 @@ static nrc_status check_cfg(const nrc_config* cfg) {
     return set_error("invalid optimiser or loss constants"), NRC_ERR_INVALID_ARG;
   if ((cfg->ema != 0 && cfg->ema != 1) || (cfg->ema && !(cfg->ema_alpha >= 0.0f && cfg->ema_alpha < 1.0f)))
     return set_error("ema must be 0 or 1 and ema_alpha in [0, 1)"), NRC_ERR_INVALID_ARG;
-  if ((cfg->refl_factor != 0 && cfg->refl_factor != 1) || cfg->reserved != 0)
-    return set_error("refl_factor must be 0 or 1 and reserved 0"), NRC_ERR_INVALID_ARG;
+  if (cfg->refl_factor != 0 && cfg->refl_factor != 1) return set_error("refl_factor must be 0 or 1"), NRC_ERR_INVALID_ARG;
+  if ((cfg->optimizer != NRC_OPT_ADAM && cfg->optimizer != NRC_OPT_SHAMPOO) || cfg->shampoo_interval < 1 ||
+      !(cfg->shampoo_eps >= 0.0f))
+    return set_error("optimizer must be NRC_OPT_ADAM or NRC_OPT_SHAMPOO, shampoo_interval >= 1, shampoo_eps >= 0"),
+           NRC_ERR_INVALID_ARG;
   return NRC_OK;
 }
 
@@ -147,6 +150,14 @@ static nrc_status check_pool(const nrc_cache* c, const float* pool, const float*
   return NRC_OK;
 }
 
+// Shampoo statistics start at zero with the step counter (nrc_create, nrc_set_state).
+static cudaError_t reset_shampoo(Cache* c, cudaStream_t st) {
+  if (c->cfg.optimizer != NRC_OPT_SHAMPOO) return cudaSuccess;
+  const size_t sh_bytes = size_t(2 * c->net.n_mats) * kShampooStatFloats * 4;
+  cudaError_t e = cudaMemsetAsync(c->sh_stats, 0, sh_bytes, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->sh_roots, 0, sh_bytes, st);
+  return e;
+}
 }  // namespace nrc
 
 
@@ -175,7 +186,9 @@ void nrc_default_config(nrc_config* cfg) {
   cfg->ema = 0;
   cfg->ema_alpha = 0.99f;
   cfg->refl_factor = 0;
-  cfg->reserved = 0;
+  cfg->optimizer = NRC_OPT_ADAM;
+  cfg->shampoo_interval = 4;
+  cfg->shampoo_eps = 1e-4f;
 }
 
 namespace nrc {
@@ -203,6 +216,10 @@ static void free_cache(nrc_cache* c) {
   cudaFree(c->wimg);
   cudaFree(c->ema);
   cudaFree(c->wimg_ema);
+  cudaFree(c->sh_g);
+  cudaFree(c->sh_stats);
+  cudaFree(c->sh_roots);
+  cudaFree(c->sh_anorm);
   cudaFree(c->partials);
   cudaFree(c->err);
   cudaFree(c->plain_buf);
@@ -241,6 +258,11 @@ nrc_status nrc_create(const nrc_config* cfg, nrc_stream stream, nrc_cache** out)
   if (e == cudaSuccess) e = cudaMalloc(&c->err, sizeof(int));
   if (e == cudaSuccess && cfg->ema) e = cudaMalloc(&c->ema, np * 4);
   if (e == cudaSuccess && cfg->ema) e = cudaMalloc(&c->wimg_ema, size_t(c->img.off[c->net.n_mats]) + 1024);
+  const size_t sh_bytes = size_t(2 * c->net.n_mats) * kShampooStatFloats * 4;
+  if (e == cudaSuccess && cfg->optimizer == NRC_OPT_SHAMPOO) e = cudaMalloc(&c->sh_g, np * 4);
+  if (e == cudaSuccess && cfg->optimizer == NRC_OPT_SHAMPOO) e = cudaMalloc(&c->sh_stats, sh_bytes);
+  if (e == cudaSuccess && cfg->optimizer == NRC_OPT_SHAMPOO) e = cudaMalloc(&c->sh_roots, sh_bytes);
+  if (e == cudaSuccess && cfg->optimizer == NRC_OPT_SHAMPOO) e = cudaMalloc(&c->sh_anorm, (np + 31) / 32 * 4);
   if (e != cudaSuccess) {
     nrc_status st = cuda_status(e, "nrc_create allocation");
     free_cache(c);
@@ -257,6 +279,7 @@ nrc_status nrc_create(const nrc_config* cfg, nrc_stream stream, nrc_cache** out)
   if (e == cudaSuccess) e = cudaMemsetAsync(c->wimg, 0, size_t(c->img.off[c->net.n_mats]) + 1024, st);
   if (e == cudaSuccess) e = launch_build_image(c, st);
   if (e == cudaSuccess) e = reset_ema(c, st);
+  if (e == cudaSuccess) e = reset_shampoo(c, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // w0 is a host temporary
   if (e != cudaSuccess) {
     nrc_status s2 = cuda_status(e, "nrc_create upload");
@@ -351,6 +374,11 @@ static nrc_status train_impl(nrc_cache* c, const float* pool, const float* targe
   else
     e = launch_train_tc(c, pool, target, n_pool, batch, a, cc, step, &n_partials, &grad_scale, st);
   if (e != cudaSuccess) return cuda_status(e, "nrc_train_step (gradient)");
+  if (c->cfg.optimizer == NRC_OPT_SHAMPOO) {
+    e = launch_shampoo(c, n_partials, grad_scale, loss_out, st);
+    c->launches += 4;
+    return cuda_status(e, "nrc_train_step (shampoo)");
+  }
   e = launch_adam(c, n_partials, grad_scale, loss_out, st);
   c->launches += 2;
   return cuda_status(e, "nrc_train_step (adam)");
@@ -458,6 +486,7 @@ nrc_status nrc_set_state(nrc_cache* c, const float* w, const float* m, const flo
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->t, &t, sizeof(t), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = launch_build_image(c, st);
   if (e == cudaSuccess) e = reset_ema(c, st);
+  if (e == cudaSuccess) e = reset_shampoo(c, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   return cuda_status(e, "nrc_set_state");
 }

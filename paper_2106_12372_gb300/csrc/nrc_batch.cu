@@ -34,6 +34,8 @@ nrc_status batch_check(nrc_cache* const* caches, int n_caches) {
     if (!caches[c]) return set_error("batched caches: cache %d is NULL", c), NRC_ERR_INVALID_ARG;
     if (caches[c]->cfg.dtype == NRC_FP32)
       return set_error("batched caches compute in FP16 or BF16"), NRC_ERR_UNSUPPORTED;
+    if (caches[c]->cfg.optimizer != NRC_OPT_ADAM)
+      return set_error("batched caches train with Adam"), NRC_ERR_UNSUPPORTED;
     if (!batch_same_cfg(caches[c]->cfg, caches[0]->cfg))
       return set_error("batched caches: cache %d differs in configuration from cache 0", c), NRC_ERR_INVALID_ARG;
     if (caches[c]->device != caches[0]->device)

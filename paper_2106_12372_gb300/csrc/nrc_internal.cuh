@@ -59,6 +59,12 @@ struct Cache {
   uint8_t* wimg = nullptr;        // 16-bit weight image (tensor-core path)
   float* ema = nullptr;           // weight average of Eq. 2 (cfg.ema), FP32 [n_params]
   uint8_t* wimg_ema = nullptr;    // its 16-bit image (what queries read when cfg.ema)
+  // Shampoo (cfg.optimizer): gradient, statistics L_l/R_l and their inverse
+  // fourth roots (each 64 x 64, block 2l = L_l, 2l+1 = R_l), per-block ||A||^2
+  float* sh_g = nullptr;
+  float* sh_stats = nullptr;
+  float* sh_roots = nullptr;
+  float* sh_anorm = nullptr;
   float* partials = nullptr;      // [max_partials][partial_stride] weight-gradient partials; loss at [n_params]
   int max_partials = 0;
   int* err = nullptr;     // device error word
@@ -142,6 +148,9 @@ cudaError_t launch_train_simt(Cache* c, const float* pool, const float* target, 
                               uint64_t a, uint64_t cc, int step, int* n_partials, cudaStream_t st);
 cudaError_t launch_adam(Cache* c, int n_partials, float grad_scale, float* loss_out, cudaStream_t st);
 cudaError_t launch_build_image(Cache* c, cudaStream_t st);
+// Shampoo step after a gradient launch (replaces launch_adam when cfg.optimizer).
+cudaError_t launch_shampoo(Cache* c, int n_partials, float grad_scale, float* loss_out, cudaStream_t st);
+constexpr size_t kShampooStatFloats = 64 * 64;  // one statistic (or root), 64 x 64
 // 16-bit image of an arbitrary FP32 weight set of c's shape into img.
 cudaError_t launch_build_image_of(const Cache* c, const float* w, uint8_t* img, cudaStream_t st);
 // What queries read: the weight average when the cache keeps one.
@@ -282,6 +291,18 @@ __host__ __device__ __forceinline__ uint32_t sw128_offset(uint32_t n, uint32_t k
 // visible, pdl_launch_dependents() lets the successor start early.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// b^t for integer t >= 0 by repeated squaring in FP32: exact for t = 1, about
+// 2 log2(t) roundings otherwise (FP64 arithmetic is slow on this part).
+__device__ __forceinline__ float pow_int(float b, long long t) {
+  float r = 1.0f;
+  while (t > 0) {
+    if (t & 1) r *= b;
+    b *= b;
+    t >>= 1;
+  }
+  return r;
+}
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
   unsigned long long t;

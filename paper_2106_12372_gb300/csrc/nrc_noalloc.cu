@@ -80,8 +80,9 @@ extern "C" nrc_status nrc_train_step_noalloc(const nrc_config* cfg, float* weigh
     return set_error("unknown loss_mode %d", cfg->loss_mode), NRC_ERR_INVALID_ARG;
   if (cfg->ema)
     return set_error("nrc_train_step_noalloc keeps no weight average (cfg->ema must be 0)"), NRC_ERR_UNSUPPORTED;
-  if ((cfg->refl_factor != 0 && cfg->refl_factor != 1) || cfg->reserved != 0)
-    return set_error("refl_factor must be 0 or 1 and reserved 0"), NRC_ERR_INVALID_ARG;
+  if (cfg->refl_factor != 0 && cfg->refl_factor != 1) return set_error("refl_factor must be 0 or 1"), NRC_ERR_INVALID_ARG;
+  if (cfg->optimizer != NRC_OPT_ADAM)
+    return set_error("nrc_train_step_noalloc trains with Adam only"), NRC_ERR_UNSUPPORTED;
   if (batch < 0 || n_pool < 0 || step_in_frame < 0) return set_error("negative size or step"), NRC_ERR_INVALID_ARG;
   if (batch == 0) return NRC_OK;
   if (batch > kMaxBatch)

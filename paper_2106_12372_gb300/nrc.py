@@ -23,6 +23,7 @@ FP32, FP16, BF16 = 0, 1, 2
 ENC_CHEAP, ENC_EXACT = 0, 1
 LOSS_LUMINANCE, LOSS_PER_CHANNEL = 0, 1
 PATH_FUSED, PATH_PLAIN = 0, 1
+OPT_ADAM, OPT_SHAMPOO = 0, 1
 DTYPES = {"fp32": FP32, "fp16": FP16, "bf16": BF16}
 
 _lock = threading.Lock()
@@ -53,7 +54,9 @@ class Config(ctypes.Structure):
         ("ema", ctypes.c_int32),
         ("ema_alpha", ctypes.c_float),
         ("refl_factor", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("optimizer", ctypes.c_int32),
+        ("shampoo_interval", ctypes.c_int32),
+        ("shampoo_eps", ctypes.c_float),
     ]
 
 
