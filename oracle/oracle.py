@@ -11,6 +11,7 @@ the paper each step follows.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -306,3 +307,118 @@ class ShampooState:
         shampoo_update(self.W, self.m, self.v, self.Ls, self.Rs, self.Ps, G, self.t, self.dims, lr=self.lr,
                        eps_rel=self.eps_rel, interval=self.interval)
         return (val, G) if want_grad else val
+
+
+# ------------------------------------------------- training-record pipeline --
+# The steps around the cache query (Sec. 3.3-3.5, the termination heuristic of
+# Sec. 3.4 "Path Termination", Eqs. 3-4), on path vertices laid out as
+# synth.make_paths writes them (24 floats per vertex).  The termination
+# decisions are taken in FP32 with the same operation order as the kernels
+# (a decision is an integer that floating point decides); the radiance sums
+# are FP64.  Readings: a vertex's spread term is sqrt(|x_{i-1} - x_i|^2 /
+# (pdf_i |cos_i|)); the rendering path ends at the first vertex n >= 2 with
+# a(x_1..x_n) > c a_0 (else at the last vertex); a training suffix restarts the
+# sum at x_n and ends at the first m > n with a(x_n..x_m) > c a_0; an unbiased
+# suffix instead continues from each vertex j >= n with probability q (the
+# bounce weighted by 1/q) and ends where the roulette stops it.
+_F32_4PI = np.float32(4.0 * math.pi)
+
+
+def _d2_f32(a, b):
+    d = (a - b).astype(np.float32)
+    return ((d[..., 0] * d[..., 0]) + (d[..., 1] * d[..., 1])) + (d[..., 2] * d[..., 2])
+
+
+def paths_terminate(vtx, width: int, height: int, camera, c: float, tile: int, ox: int, oy: int, phase: int,
+                    rr_q: float):
+    """Returns (n [P], render_emitted [P,3], render_throughput [P,3], tiles) where tiles
+    is a list of (pixel, n, m, unbiased) per tile (pixel -1: no training path)."""
+    vtx = np.asarray(vtx, dtype=np.float32)
+    P, K, _ = vtx.shape
+    c32 = np.float32(c)
+    x = vtx[:, :, 0:3]
+    cam = np.asarray(camera, dtype=np.float32)
+    a0 = _d2_f32(x[:, 0], cam[None, :]) / (_F32_4PI * vtx[:, 0, 15])
+    thr = c32 * a0
+    # spread term of vertex j >= 1 (the edge x_{j-1} -> x_j)
+    s = np.zeros((P, K), dtype=np.float32)
+    for j in range(1, K):
+        s[:, j] = np.sqrt(_d2_f32(x[:, j - 1], x[:, j]) / (vtx[:, j, 14] * vtx[:, j, 15]))
+    n = np.full(P, K - 1, dtype=np.int64)
+    done = np.zeros(P, dtype=bool)
+    acc = np.zeros(P, dtype=np.float32)
+    for j in range(1, K):
+        acc = acc + s[:, j]
+        hit = (~done) & ((acc * acc) > thr)
+        n[hit] = j
+        done |= hit
+    f = vtx[:, :, 19:22].astype(np.float64)
+    le = vtx[:, :, 16:19].astype(np.float64)
+    E = np.zeros((P, 3))
+    T = np.ones((P, 3))
+    Tn = np.zeros((P, 3))
+    for j in range(K):
+        live = j <= n
+        E[live] += T[live] * le[live, j]
+        Tn[j == n] = T[j == n]
+        T = T * f[:, j]
+    tiles_x, tiles_y = -(-width // tile), -(-height // tile)
+    tiles = []
+    for t in range(tiles_x * tiles_y):
+        ty, tx = divmod(t, tiles_x)
+        px, py = tx * tile + ox, ty * tile + oy
+        if px >= width or py >= height:
+            tiles.append((-1, 0, 0, 0))
+            continue
+        p = py * width + px
+        nn = int(n[p])
+        unb = phase >= 0 and t % 16 == phase
+        m = K - 1
+        if unb:
+            for j in range(nn, K):
+                if j == K - 1 or not (vtx[p, j, 22] < np.float32(rr_q)):
+                    m = j
+                    break
+        else:
+            a = np.float32(0.0)
+            for j in range(nn + 1, K):
+                a = np.float32(a + s[p, j])
+                if np.float32(a * a) > thr[p]:
+                    m = j
+                    break
+        tiles.append((p, nn, m, int(unb)))
+    return n, E, Tn, tiles
+
+
+def paths_records(vtx, tiles, tail_rgb, rr_q: float):
+    """Training records and self-training targets (Sec. 3.3): for each training
+    path (tiles in order) the vertices 0 .. m-1 with the reflected radiance
+    transported back from the tail (the cache's value at x_m, or 0 where the
+    roulette ended an unbiased suffix).  Returns (records [N,16] float32, targets [N,3])."""
+    vtx = np.asarray(vtx, dtype=np.float32)
+    recs, tgts = [], []
+    for t, (p, n, m, unb) in enumerate(tiles):
+        if p < 0:
+            continue
+        L = np.zeros(3) if unb else np.asarray(tail_rgb[t], dtype=np.float64)
+        out = []
+        for j in range(m - 1, -1, -1):
+            w = vtx[p, j, 19:22].astype(np.float64)
+            if unb and j >= n:
+                w = w / np.float64(np.float32(rr_q))
+            L = w * (vtx[p, j + 1, 16:19].astype(np.float64) + L)
+            out.append((j, L.copy()))
+        for j, L in reversed(out):
+            r = np.zeros(16, dtype=np.float32)
+            r[0:14] = vtx[p, j, 0:14]
+            recs.append(r)
+            tgts.append(L)
+    if not recs:
+        return np.zeros((0, 16), np.float32), np.zeros((0, 3))
+    return np.array(recs, dtype=np.float32), np.array(tgts)
+
+
+def paths_composite(emitted, throughput, rgb):
+    """Pixel radiance: emitted light along the rendering path plus the path
+    throughput times the cache's value at its terminal vertex."""
+    return np.asarray(emitted, np.float64) + np.asarray(throughput, np.float64) * np.asarray(rgb, np.float64)

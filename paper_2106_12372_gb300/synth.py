@@ -166,3 +166,83 @@ def frame_seed(base_seed: int, frame: int) -> int:
     """The 64-bit seed of frame ``frame`` (drives the training-record shuffle)."""
     _, out = splitmix64_next((stream_state(base_seed, STREAM_FRAMES) + frame * GOLDEN_GAMMA) & MASK64)
     return out
+
+
+# ------------------------------------------------------------ synthetic paths
+# Stand-in for the path tracer that produces the cache's queries and training
+# records: cosine-sampled random walks inside the unit cube [0,1]^3 (inward
+# normals) seen from a pinhole camera, with an emissive patch on the ceiling.
+# Per vertex the generator records what a path tracer knows there.  It draws
+# with numpy's PCG64 (O'Neill 2014) and holds none of the method's arithmetic:
+# termination, transport and record assembly are the method's steps and live
+# in the kernels (and, independently, in the oracle).
+PATH_VERTEX_FLOATS = 24
+# layout of one vertex (float32): 0-2 position, 3-4 direction towards the
+# previous vertex and 5-6 normal (both as (theta/pi, phi/(2 pi))), 7 roughness,
+# 8-10 diffuse albedo, 11-13 specular albedo (0-13: the query record's first 14
+# floats), 14 pdf (solid angle) of the direction that reached this vertex, 15
+# |cos| between that direction and the normal here, 16-18 emitted radiance,
+# 19-21 throughput weight of the bounce leaving this vertex (BSDF cos / pdf),
+# 22 a uniform for Russian roulette, 23 zero.
+PATH_CAMERA = (0.5, 0.5, 0.02)
+
+
+def _spherical01(d: np.ndarray) -> np.ndarray:
+    theta = np.arccos(np.clip(d[:, 2], -1.0, 1.0))
+    phi = np.mod(np.arctan2(d[:, 1], d[:, 0]), 2.0 * math.pi)
+    return np.stack([theta / math.pi, phi / (2.0 * math.pi)], axis=1)
+
+
+def _cube_hit(o: np.ndarray, d: np.ndarray):
+    """First wall of the unit cube hit from inside: point, axis, inward normal."""
+    with np.errstate(divide="ignore", invalid="ignore"):
+        t = np.where(d > 0, (1.0 - o) / d, np.where(d < 0, -o / d, np.inf))
+    axis = np.argmin(t, axis=1)
+    tm = t[np.arange(len(o)), axis]
+    x = np.clip(o + tm[:, None] * d, 0.0, 1.0)
+    nrm = np.zeros_like(o)
+    nrm[np.arange(len(o)), axis] = -np.sign(d[np.arange(len(o)), axis])
+    return x, axis, nrm
+
+
+def make_paths(width: int, height: int, n_vertices: int = 10, seed: int = BASE_SEED) -> np.ndarray:
+    """Paths of a width x height viewport: float32 [height*width, n_vertices, 24] (row-major pixels)."""
+    rng = np.random.default_rng(seed)
+    P = width * height
+    cam = np.array(PATH_CAMERA)
+    py, px = np.divmod(np.arange(P), width)
+    tan = math.tan(math.radians(35.0))
+    d = np.stack([((px + 0.5) / width - 0.5) * 2 * tan * width / height, ((py + 0.5) / height - 0.5) * 2 * tan,
+                  np.ones(P)], axis=1)
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    o = np.repeat(cam[None, :], P, axis=0)
+    out = np.zeros((P, n_vertices, PATH_VERTEX_FLOATS), dtype=np.float64)
+    pdf_in = np.ones(P)
+    for k in range(n_vertices):
+        x, axis, nrm = _cube_hit(o, d)
+        out[:, k, 0:3] = x
+        out[:, k, 3:5] = _spherical01(-d)
+        out[:, k, 5:7] = _spherical01(nrm)
+        cell = (np.floor(4 * x[:, 0]) + np.floor(4 * x[:, 1]) + np.floor(4 * x[:, 2])) % 2
+        albedo = np.where(cell[:, None] > 0, [0.75, 0.62, 0.48], [0.32, 0.42, 0.66]) * (0.7 + 0.1 * axis)[:, None]
+        out[:, k, 7] = 0.2 + 0.6 * np.mod(7 * x[:, 0] + 3 * x[:, 1] + 5 * x[:, 2], 1.0)
+        out[:, k, 8:11] = albedo
+        out[:, k, 11:14] = 0.04
+        out[:, k, 14] = pdf_in
+        out[:, k, 15] = np.abs(np.sum(d * nrm, axis=1))
+        lamp = (axis == 1) & (nrm[:, 1] < 0) & (np.abs(x[:, 0] - 0.5) < 0.2) & (np.abs(x[:, 2] - 0.5) < 0.2)
+        out[:, k, 16:19] = np.where(lamp[:, None], [6.0, 6.0, 5.0], 0.0)
+        out[:, k, 19:22] = albedo  # Lambertian, cosine-weighted sampling: f cos / pdf = albedo
+        out[:, k, 22] = rng.random(P)
+        # cosine-weighted direction about the (axis-aligned) normal
+        u1, u2 = rng.random(P), rng.random(P)
+        r, ph = np.sqrt(u1), 2 * math.pi * u2
+        loc = np.stack([r * np.cos(ph), r * np.sin(ph), np.sqrt(np.maximum(0.0, 1.0 - u1))], axis=1)
+        t1 = np.zeros_like(nrm)
+        t1[np.arange(P), (axis + 1) % 3] = 1.0
+        t2 = np.cross(nrm, t1)
+        dn = loc[:, 0:1] * t1 + loc[:, 1:2] * t2 + loc[:, 2:3] * nrm
+        pdf_in = loc[:, 2] / math.pi
+        o = x + 1e-7 * nrm
+        d = dn / np.linalg.norm(dn, axis=1, keepdims=True)
+    return out.astype(np.float32)
