@@ -425,6 +425,76 @@ NRC_API nrc_status nrc_get_ema(nrc_cache* cache, float* ema, nrc_stream stream);
  * 16-bit image the queries read (synchronises the stream). */
 NRC_API nrc_status nrc_set_ema(nrc_cache* cache, const float* ema, nrc_stream stream);
 
+/* ----------------------------------------------------------------------
+ * Training-record pipeline around the cache query (Sec. 3.3 self-training,
+ * Sec. 3.4 path termination with the area-spread heuristic, Eqs. 3-4,
+ * Sec. 3.5 one training path per screen tile).  Input: the vertices a path
+ * tracer produced for every pixel, n_vertices per pixel, 24 floats each:
+ *   0-2 position x_i, 3-4 direction towards x_{i-1} and 5-6 normal (both
+ *   (theta/pi, phi/(2 pi))), 7 roughness, 8-10 diffuse and 11-13 specular
+ *   albedo (0-13 are the query record's first 14 floats), 14 pdf (solid angle)
+ *   of the direction that reached x_i, 15 |cos| of that direction with the
+ *   normal at x_i, 16-18 emitted radiance, 19-21 throughput weight of the
+ *   bounce leaving x_i (BSDF cos / pdf), 22 a uniform for Russian roulette,
+ *   23 unused.
+ * Decisions: the rendering path ends at the first x_n (n >= 1, 0-based) whose
+ * spread (sum_{i=1..n} sqrt(|x_{i-1} - x_i|^2 / (pdf_i cos_i)))^2 exceeds
+ * c a_0, a_0 = |camera - x_0|^2 / (4 pi cos_0), or at the last vertex; every
+ * tile x tile block of pixels has one training path, the pixel at offset
+ * (tile_ox, tile_oy); its suffix restarts the sum at x_n and ends at the first
+ * x_m past the threshold -- or, in tiles t with t % 16 == unbiased_phase,
+ * continues from each vertex j >= n with probability rr_survive (roulette
+ * uniform < rr_survive; weight 1/rr_survive) and ends where it stops.  These
+ * decisions are computed with round-to-nearest FP32 operations in a fixed
+ * order (include no fused multiply-adds), hence reproducible. */
+typedef struct nrc_paths {
+  const float* vertices; /* device, [width*height][n_vertices][24], pixels row-major, 16-byte aligned */
+  int32_t width, height, n_vertices; /* 2 <= n_vertices <= 64 */
+  float camera[3];       /* x_{-1}: the camera position */
+} nrc_paths;
+
+typedef struct nrc_path_params {
+  float c;               /* spread threshold; 0.01 (Sec. 3.4) */
+  int32_t tile;          /* side of a training tile in pixels */
+  int32_t tile_ox, tile_oy; /* this frame's offset of the training pixel in each tile, in [0, tile) */
+  int32_t unbiased_phase; /* tiles with t % 16 == phase get a roulette-only suffix (u = 1/16); -1: none */
+  float rr_survive;      /* roulette survival probability of those suffixes; 0.8 */
+} nrc_path_params;
+
+/* Number of training tiles, ceil(width/tile) * ceil(height/tile) (0 on bad sizes). */
+NRC_API int64_t nrc_paths_tile_count(int32_t width, int32_t height, int32_t tile);
+
+/* Tile side for the next frame so that the training records approach
+ * `target` (Sec. 3.5's adaptive tiling): tile * sqrt(generated / target),
+ * rounded, in [1, 256]. */
+NRC_API int32_t nrc_paths_adapt_tile(int32_t tile, int64_t generated, int64_t target);
+
+/* Terminates every pixel's rendering path and picks the training paths.
+ * Outputs (device, caller-owned): render_queries [pixels][16] (the record of
+ * each terminal vertex, for nrc_infer), render_emitted [pixels][3] (emitted
+ * light along the path, throughput-weighted), render_throughput [pixels][3]
+ * (throughput from the camera to the terminal vertex), tiles [n_tiles][4]
+ * int32 {pixel or -1, n, m, unbiased} and tail_queries [n_tiles][16] (the
+ * record of x_m, the training path's self-training query). */
+NRC_API nrc_status nrc_paths_terminate(const nrc_paths* paths, const nrc_path_params* params,
+                                       float* render_queries, float* render_emitted, float* render_throughput,
+                                       int32_t* tiles, float* tail_queries, nrc_stream stream);
+
+/* Self-training records (Sec. 3.3): for each training path, in tile order, the
+ * records of x_0 .. x_{m-1} with targets L_j = w_j (Le_{j+1} + L_{j+1}) from
+ * L_m = tail_rgb[t] (the cache's value at x_m; 0 where the roulette ended an
+ * unbiased suffix).  Writes min(total, max_records) records into pool
+ * [max][16] and targets [max][3]; offsets [n_tiles] (device int64 scratch)
+ * receives each path's first record, *count (device int64) the total. */
+NRC_API nrc_status nrc_paths_records(const nrc_paths* paths, const nrc_path_params* params, const int32_t* tiles,
+                                     const float* tail_rgb, float* pool, float* targets, int64_t max_records,
+                                     int64_t* offsets, int64_t* count, nrc_stream stream);
+
+/* Pixel radiance: image = render_emitted + render_throughput * rgb (rgb: the
+ * cache's value at each terminal vertex), all [n][3] device arrays. */
+NRC_API nrc_status nrc_paths_composite(const float* render_emitted, const float* render_throughput,
+                                       const float* rgb, int64_t n, float* image, nrc_stream stream);
+
 /* Why the last failing call on this thread failed ("" if none). */
 NRC_API const char* nrc_last_error_string(void);
 

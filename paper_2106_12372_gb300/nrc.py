@@ -142,6 +142,11 @@ def lib() -> ctypes.CDLL:
             "nrc_batch_autotune": (i32, [P, P, P, P, P, P]),
             "nrc_batch_set_train_tiles": (i32, [P, i32]),
             "nrc_get_ema": (i32, [P, P, P]),
+            "nrc_paths_tile_count": (i64, [i32, i32, i32]),
+            "nrc_paths_adapt_tile": (i32, [i32, i64, i64]),
+            "nrc_paths_terminate": (i32, [P, P, P, P, P, P, P, P]),
+            "nrc_paths_records": (i32, [P, P, P, P, P, P, i64, P, P, P]),
+            "nrc_paths_composite": (i32, [P, P, P, i64, P, P]),
             "nrc_set_ema": (i32, [P, P, P]),
             "nrc_server_default_config": (None, [P]),
             "nrc_now_ns": (i64, []),
@@ -481,3 +486,68 @@ class Server:
         out = ServerInfo()
         _check(lib().nrc_server_query(self._h, ctypes.byref(out)))
         return out
+
+
+class _Paths(ctypes.Structure):
+    _fields_ = [("vertices", ctypes.c_void_p), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("n_vertices", ctypes.c_int32), ("camera", ctypes.c_float * 3)]
+
+
+class PathParams(ctypes.Structure):
+    _fields_ = [("c", ctypes.c_float), ("tile", ctypes.c_int32), ("tile_ox", ctypes.c_int32),
+                ("tile_oy", ctypes.c_int32), ("unbiased_phase", ctypes.c_int32), ("rr_survive", ctypes.c_float)]
+
+
+def paths_tile_count(width: int, height: int, tile: int) -> int:
+    return lib().nrc_paths_tile_count(width, height, tile)
+
+
+def paths_adapt_tile(tile: int, generated: int, target: int) -> int:
+    return lib().nrc_paths_adapt_tile(tile, generated, target)
+
+
+def _paths(vertices, width, height, camera):
+    return _Paths(_ptr(vertices), width, height, vertices.shape[1], (ctypes.c_float * 3)(*camera))
+
+
+def paths_terminate(vertices, width: int, height: int, camera, params: PathParams, stream=None):
+    """(render_queries, render_emitted, render_throughput, tiles, tail_queries) as device tensors."""
+    import torch
+
+    d = vertices.device
+    P = width * height
+    nt = paths_tile_count(width, height, params.tile)
+    rq = torch.empty((P, 16), device=d)
+    em = torch.empty((P, 3), device=d)
+    tp = torch.empty((P, 3), device=d)
+    tiles = torch.empty((nt, 4), dtype=torch.int32, device=d)
+    tq = torch.zeros((nt, 16), device=d)
+    ps = _paths(vertices, width, height, camera)
+    _check(lib().nrc_paths_terminate(ctypes.byref(ps), ctypes.byref(params), _ptr(rq), _ptr(em), _ptr(tp),
+                                     _ptr(tiles), _ptr(tq), _stream(stream)))
+    return rq, em, tp, tiles, tq
+
+
+def paths_records(vertices, width: int, height: int, camera, params: PathParams, tiles, tail_rgb, max_records: int,
+                  stream=None):
+    """(pool [max,16], targets [max,3], count device int64 [1])."""
+    import torch
+
+    d = vertices.device
+    pool = torch.zeros((max_records, 16), device=d)
+    tg = torch.zeros((max_records, 3), device=d)
+    offsets = torch.empty(tiles.shape[0], dtype=torch.int64, device=d)
+    count = torch.zeros(1, dtype=torch.int64, device=d)
+    ps = _paths(vertices, width, height, camera)
+    _check(lib().nrc_paths_records(ctypes.byref(ps), ctypes.byref(params), _ptr(tiles), _ptr(tail_rgb), _ptr(pool),
+                                   _ptr(tg), max_records, _ptr(offsets), _ptr(count), _stream(stream)))
+    return pool, tg, count
+
+
+def paths_composite(emitted, throughput, rgb, stream=None):
+    import torch
+
+    img = torch.empty_like(emitted)
+    _check(lib().nrc_paths_composite(_ptr(emitted), _ptr(throughput), _ptr(rgb), emitted.shape[0], _ptr(img),
+                                     _stream(stream)))
+    return img

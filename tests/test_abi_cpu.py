@@ -61,3 +61,17 @@ def test_bad_arguments_fail_on_the_host(L):
     assert L.nrc_gather(None, None, 100, 0, 0, 0, None, None, None) == nrc.NRC_OK  # empty batch: no-op
     assert L.nrc_destroy(None) == nrc.NRC_OK
     assert L.nrc_param_count(None) == 0
+
+
+def test_path_tiling_helpers_on_the_host():
+    from paper_2106_12372_gb300 import build, nrc
+
+    build.build()
+    assert nrc.paths_tile_count(1920, 1080, 8) == 240 * 135
+    assert nrc.paths_tile_count(37, 21, 8) == 5 * 3
+    assert nrc.paths_tile_count(0, 21, 8) == 0
+    # records scale with the number of tiles ~ 1 / tile^2: four times the target doubles the side
+    assert nrc.paths_adapt_tile(8, 4 * 65536, 65536) == 16
+    assert nrc.paths_adapt_tile(8, 65536 // 4, 65536) == 4
+    assert nrc.paths_adapt_tile(8, 65536, 65536) == 8
+    assert nrc.paths_adapt_tile(1, 1, 10 ** 9) == 1 and nrc.paths_adapt_tile(200, 10 ** 9, 1) == 256

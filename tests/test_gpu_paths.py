@@ -1,0 +1,110 @@
+"""GPU parity of the training-record pipeline (Sec. 3.3-3.5; termination
+heuristic Eqs. 3-4) against the oracle on seeded synthetic paths.
+
+Termination decisions, the training tiles and every record are bit-exact (both
+sides decide in FP32 in the same operation order); emitted sums, throughputs,
+targets and the composite agree to 1e-5 (FP32 against FP64, floored at the rms).
+"""
+import numpy as np
+import pytest
+
+from paper_2106_12372_gb300 import synth
+from parity import rel_err
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU containers
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+from oracle import oracle as O  # noqa: E402
+from paper_2106_12372_gb300 import build, nrc  # noqa: E402
+
+DEV = torch.device("cuda:0")
+DIMS = synth.layer_dims()
+W, H, K = 97, 61, 10
+
+
+@pytest.fixture(scope="module")
+def scene():
+    build.build()
+    v = synth.make_paths(W, H, K, seed=21)
+    return v, torch.from_numpy(v).to(DEV)
+
+
+def _params(c=0.01, tile=8, ox=3, oy=5, phase=7, q=0.8):
+    return nrc.PathParams(c, tile, ox, oy, phase, q)
+
+
+def _record(vtx_row):
+    r = np.zeros(16, np.float32)
+    r[:14] = vtx_row[:14]
+    return r
+
+
+@pytest.mark.parametrize("c,tile,ox,oy,phase", [(0.01, 8, 3, 5, 7), (0.1, 5, 0, 4, -1), (0.001, 16, 15, 15, 0)])
+def test_termination_and_tiles_match_oracle(scene, c, tile, ox, oy, phase):
+    v, V = scene
+    rq, em, tp, tiles, tq = nrc.paths_terminate(V, W, H, synth.PATH_CAMERA, _params(c, tile, ox, oy, phase))
+    n, E, T, ref_tiles = O.paths_terminate(v, W, H, synth.PATH_CAMERA, c, tile, ox, oy, phase, 0.8)
+    ref_rq = np.stack([_record(v[p, n[p]]) for p in range(W * H)])
+    assert np.array_equal(rq.cpu().numpy().view(np.uint32), ref_rq.view(np.uint32))
+    assert np.array_equal(tiles.cpu().numpy(), np.array(ref_tiles, dtype=np.int32))
+    tqh = tq.cpu().numpy()
+    for t, (p, nn, m, unb) in enumerate(ref_tiles):
+        if p >= 0:
+            assert np.array_equal(tqh[t].view(np.uint32), _record(v[p, m]).view(np.uint32))
+    assert rel_err(em.cpu().numpy(), E).max() <= 1e-5
+    assert rel_err(tp.cpu().numpy(), T).max() <= 1e-5
+    assert (np.array(ref_tiles)[:, 0] >= 0).sum() > 10 and 0 < n.min() and n.max() <= K - 1
+
+
+def test_records_and_targets_match_oracle(scene):
+    v, V = scene
+    prm = _params()
+    _, _, _, tiles, tq = nrc.paths_terminate(V, W, H, synth.PATH_CAMERA, prm)
+    _, _, _, ref_tiles = O.paths_terminate(v, W, H, synth.PATH_CAMERA, 0.01, 8, 3, 5, 7, 0.8)
+    w0 = synth.xavier_weights(DIMS, seed=22)
+    tail = O.infer(w0, DIMS, tq.cpu().numpy())  # the cache's values at the tails (FP64 oracle)
+    ref_rec, ref_tg = O.paths_records(v, ref_tiles, tail, 0.8)
+    pool, tg, count = nrc.paths_records(V, W, H, synth.PATH_CAMERA, prm, tiles,
+                                        torch.from_numpy(tail.astype(np.float32)).to(DEV), 4096)
+    N = len(ref_rec)
+    assert count.item() == N and N > 50
+    assert np.array_equal(pool[:N].cpu().numpy().view(np.uint32), ref_rec.view(np.uint32))
+    assert rel_err(tg[:N].cpu().numpy(), ref_tg).max() <= 1e-5
+    assert not pool[N:].any()
+    # truncation: the first max_records are written, the count is the total
+    pool2, tg2, count2 = nrc.paths_records(V, W, H, synth.PATH_CAMERA, prm, tiles,
+                                           torch.from_numpy(tail.astype(np.float32)).to(DEV), N // 3)
+    assert count2.item() == N
+    assert torch.equal(pool2, pool[:N // 3]) and torch.equal(tg2, tg[:N // 3])
+
+
+def test_composite_matches_oracle(scene):
+    v, V = scene
+    _, em, tp, _, _ = nrc.paths_terminate(V, W, H, synth.PATH_CAMERA, _params())
+    rgb = np.random.default_rng(23).uniform(0, 2, size=(W * H, 3)).astype(np.float32)
+    img = nrc.paths_composite(em, tp, torch.from_numpy(rgb).to(DEV)).cpu().numpy()
+    ref = O.paths_composite(em.cpu().numpy(), tp.cpu().numpy(), rgb)
+    assert rel_err(img, ref).max() <= 1e-6
+
+
+def test_frame_through_the_cache(scene):
+    v, V = scene
+    cache = nrc.Cache(dtype="fp16", seed=24)
+    tile = 4
+    for f in range(6):
+        prm = _params(tile=tile, ox=f % tile, oy=(3 * f) % tile, phase=f % 16)
+        rq, em, tp, tiles, tq = nrc.paths_terminate(V, W, H, synth.PATH_CAMERA, prm)
+        rgb = cache.infer(rq)
+        tail = cache.infer(tq)
+        pool, tg, count = nrc.paths_records(V, W, H, synth.PATH_CAMERA, prm, tiles, tail, 1 << 14)
+        n = int(count.item())
+        assert 0 < n <= 1 << 14
+        batch = n // 4
+        cache.frame(rq[:0], rgb[:0], pool[:n], tg[:n], batch, 4, synth.frame_seed(25, f))
+        img = nrc.paths_composite(em, tp, rgb)
+        assert torch.isfinite(img).all()
+        tile = nrc.paths_adapt_tile(tile, n, 2048)
+    cache.check_error()
