@@ -300,6 +300,47 @@ def run_shampoo(pool, tgt, dtype: str, frames: int, flush):
     return out
 
 
+def run_precision(queries, flush, frames: int = 30):
+    """Query time of the 1080p frame per arithmetic type, and the per-output
+    error against the FP64 oracle on a 2,000-query sample (median and max,
+    relative to the sample rms floor)."""
+    import numpy as np
+    import torch
+
+    from oracle import oracle as O
+    from paper_2106_12372_gb300 import nrc, synth
+
+    dims = synth.layer_dims()
+    w0 = synth.xavier_weights(dims, seed=2106)
+    sample = queries[0][:2000]
+    ref = O.infer(w0, dims, sample.cpu().numpy())
+    tau = np.sqrt(np.mean(ref ** 2))
+    out = {}
+    st = torch.cuda.current_stream()
+    rgb = torch.empty((queries[0].shape[0], 3), device=queries[0].device)
+    for dt in ("fp32", "bf16", "fp16", "fp8"):
+        c = nrc.Cache(dtype=dt, seed=2106)
+        c.set_state(w0)
+        got = c.infer(sample).cpu().numpy()
+        err = np.abs(got - ref) / np.maximum(np.abs(ref), tau)
+        for k in range(3):
+            c.infer(queries[k % 2], rgb)
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(frames if dt != "fp32" else 5)]
+        for k, e in enumerate(ev):
+            flush.zero_()
+            e[0].record(st)
+            c.infer(queries[k % 2], rgb)
+            e[1].record(st)
+        torch.cuda.synchronize()
+        c.check_error()
+        ms = float(np.median([e[0].elapsed_time(e[1]) for e in ev]))
+        out[dt] = {"infer_ms": ms, "tflops": FLOP_QUERY * N_QUERIES / (ms / 1e3) / 1e12,
+                   "err_median": float(np.median(err)), "err_max": float(err.max())}
+        c.close()
+    out["workload"] = "1080p query batch per dtype (FP32: SIMT parity path); error against the FP64 oracle"
+    return out
+
+
 def run_serving(queries, dtype: str, seconds: float):
     """Eight viewports (4 x 1920x1080, 4 x 3840x2160) with Poisson frame
     arrivals at 30-120 Hz each (rates seeded), served by the continuous-
@@ -456,11 +497,12 @@ def run_gpu(args):
             plain_ms.append(pev[0].elapsed_time(pev[1]))
     plain.close()
 
-    batched = serving = shampoo = None
+    batched = serving = shampoo = precision = None
     if not args.no_extras and ws == 1 and args.dtype != "fp32":
         batched = run_batched(queries, args.dtype, 30, flush)
         serving = run_serving(queries, args.dtype, args.serve_seconds)
         shampoo = run_shampoo(pool, tgt, args.dtype, 30, flush)
+        precision = run_precision(queries, flush)
 
     # end to end: host (pinned) buffers through nrc_frame_host, copies inside the timed region
     qh = torch.from_numpy(synth.make_records(N_QUERIES, seed=seed + 7)).pin_memory()
@@ -504,6 +546,7 @@ def run_gpu(args):
         "batched_caches": batched,
         "serving": serving,
         "shampoo": shampoo,
+        "precision": precision,
         "roofline": {"kernel": "k_infer_tc (fused encode + 6 tcgen05 layers)", "bound": "tensor", "achieved": achieved,
                      "peak": burst, "unit": "TFLOP/s", "frac": achieved / burst, "traffic": infer_traffic(),
                      "peak_source": f"{src} bf16 dense burst (fp16 peak = bf16 peak)"},

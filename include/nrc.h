@@ -70,8 +70,14 @@ typedef enum nrc_status {
 
 /* Arithmetic type of the MLP's matrix products.  NRC_FP32: FP32 SIMT FMA
  * (the parity path).  NRC_FP16 / NRC_BF16: tcgen05 tensor-core products with
- * FP32 accumulation; master weights, Adam moments and the loss stay FP32. */
-enum { NRC_FP32 = 0, NRC_FP16 = 1, NRC_BF16 = 2 };
+ * FP32 accumulation; master weights, Adam moments and the loss stay FP32.
+ * NRC_FP8: queries with E4M3 operands (tcgen05 kind::f8f6f4, FP32
+ * accumulation): each weight matrix scaled by a power of two from its amax,
+ * the encoded inputs by 128, and every hidden layer's activations of a row by
+ * a power of two from that row's amax (undone exactly in the next epilogue);
+ * training as NRC_FP16.  Batched caches, the server and the allocation-free
+ * step do not take it. */
+enum { NRC_FP32 = 0, NRC_FP16 = 1, NRC_BF16 = 2, NRC_FP8 = 3 };
 
 /* Encoding primitives (Sec. 5, Fig. 7): CHEAP replaces the sine by the
  * triangle wave tri(x) = 2|x mod 2 - 1| - 1 and the one-blob Gaussian by the

@@ -352,7 +352,7 @@ cudaError_t launch_shampoo(Cache* c, int n_partials, float grad_scale, float* lo
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   float* ema = k.ema ? c->ema : nullptr;
-  if (k.dtype == NRC_FP16)
+  if (fp16_like(k.dtype))
     k_shampoo_update<1><<<net.n_mats, kShThreads, smem_update, st>>>(net, c->img, c->w, c->m, c->sh_roots, c->sh_anorm,
                                                                      (const long long*)c->t, k.lr, k.beta1, c->wimg,
                                                                      ema, c->wimg_ema, k.ema_alpha);

@@ -550,7 +550,7 @@ cudaError_t launch_adam(Cache* c, int n_partials, float grad_scale, float* loss_
   const NetShape& net = c->net;
   const ImageShape& img = c->img;
   float* ema = k.ema ? c->ema : nullptr;
-  if (k.dtype == NRC_FP16)
+  if (fp16_like(k.dtype))
     return cudaLaunchKernelEx(&lc, k_adam<1>, c->w, c->m, c->v, (const long long*)c->t, (const float*)c->partials,
                               n_partials, net, img, c->wimg, grad_scale, k.lr, k.beta1, k.beta2, k.adam_eps, loss_out,
                               ema, c->wimg_ema, k.ema_alpha);
@@ -609,7 +609,7 @@ cudaError_t launch_build_image_of(const Cache* c, const float* w, uint8_t* img, 
   if (e != cudaSuccess) return e;
   const int threads = 256;
   const int blocks = (c->net.n_params + threads - 1) / threads;
-  if (c->cfg.dtype == NRC_FP16)
+  if (fp16_like(c->cfg.dtype))
     k_build_image<1><<<blocks, threads, 0, st>>>(w, c->net, c->img, img);
   else
     k_build_image<2><<<blocks, threads, 0, st>>>(w, c->net, c->img, img);

@@ -348,6 +348,202 @@ __global__ void __launch_bounds__(kInferThreads, 1) k_infer_batched(const __grid
   }
 }
 
+// ------------------------------------------------------------ FP8 queries
+// The query kernel with E4M3 operands (dtype NRC_FP8): the same slots, record
+// staging and TMEM columns as k_infer_tc, with 16 of the 32 activation columns
+// used (4 E4M3 values per column) and two K = 32 MMAs per layer.  Scales (all
+// powers of two, so undone exactly): weights of matrix l by s_l (from its
+// amax, in the image), the encoded inputs by 128, and each row's hidden
+// activations by a factor c from that row's amax that puts it in [128, 256);
+// the thread keeps 1/(product of its row's scales) to rescale the output.
+// Byte offset of matrix l in the E4M3 image: each matrix takes half its bytes
+// in the 16-bit image (rows padded to 16, 64 inputs), rounded up to 1 KB.
+__host__ __device__ __forceinline__ int img8_offset_of(const ImageShape& img, int l) {
+  int off = 0;
+  for (int j = 0; j < l; ++j) off += ((img.off[j + 1] - img.off[j]) / 2 + 1023) & ~1023;
+  return off;
+}
+
+__device__ __forceinline__ uint32_t sw64_offset(uint32_t n, uint32_t k) {
+  return (n >> 3) * 512u + (n & 7u) * 64u + ((((k >> 4) ^ (n >> 1)) & 3u) << 4) + (k & 15u);
+}
+
+// 2^(7 - floor(log2 a)) as (scale, 1/scale) for a > 0 normal; (1, 1) for a == 0
+__device__ __forceinline__ void pow2_scale(float a, float& s, float& inv) {
+  const int eb = int((__float_as_uint(a) >> 23) & 0xFFu);
+  if (eb == 0) {
+    s = inv = 1.0f;
+    return;
+  }
+  const int sb = min(254, max(1, 261 - eb));
+  s = __uint_as_float(uint32_t(sb) << 23);
+  inv = __uint_as_float(uint32_t(254 - sb) << 23);
+}
+
+// One block per matrix: amax -> scale -> E4M3 image (rows padded with zeros).
+__global__ void k_build_image_fp8(const float* __restrict__ w, const __grid_constant__ NetShape net,
+                                  const __grid_constant__ ImageShape img, uint8_t* __restrict__ img8, int img8_bytes) {
+  __shared__ float red[8];
+  const int l = blockIdx.x;
+  const int n_out = net.dims[l + 1], n_in = net.dims[l];
+  const float* wl = w + net.w_off[l];
+  float a = 0.0f;
+  for (int e = threadIdx.x; e < n_out * n_in; e += blockDim.x) a = fmaxf(a, fabsf(wl[e]));
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) a = fmaxf(a, __shfl_down_sync(0xffffffffu, a, off));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+  __syncthreads();
+  a = 0.0f;
+  for (int k = 0; k < int(blockDim.x >> 5); ++k) a = fmaxf(a, red[k]);
+  float s, inv;
+  pow2_scale(a, s, inv);
+  uint8_t* dst = img8 + img8_offset_of(img, l);
+  for (int e = threadIdx.x; e < img.rows[l] * n_in; e += blockDim.x) {
+    const int o = e / n_in, i = e % n_in;
+    const float x = o < n_out ? wl[o * n_in + i] * s : 0.0f;
+    dst[sw64_offset(o, i)] = uint8_t(pack_e4m3x2<false>(x, 0.0f) & 0xFFu);
+  }
+  if (threadIdx.x == 0) reinterpret_cast<float*>(img8 + img8_bytes)[l] = inv;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kInferThreads, 1) k_infer_fp8(const __grid_constant__ InferParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ uint64_t bar_w;
+  __shared__ uint64_t bar_mma[kSlots];
+  __shared__ uint32_t tmem_base_sh;
+  uint8_t* sw = align1024(smem_raw);
+  const int img_alloc = (p.img_bytes + kImg8ScaleBytes + 1023) & ~1023;
+  uint8_t* recs = sw + img_alloc;
+  const float* inv_sw = reinterpret_cast<const float*>(sw + p.img_bytes);
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  const int slot = tid >> 7;
+  const int rit = tid & 127;
+  if (warp == 0) {
+    tmem_alloc(&tmem_base_sh, kTmemCols);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    mbar_init(&bar_w, 1);
+    for (int s = 0; s < kSlots; ++s) mbar_init(&bar_mma[s], 1);
+    fence_barrier_init();
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_base_sh;
+  if (tid == 0) {
+    const uint32_t bytes = uint32_t(p.img_bytes) + uint32_t(kImg8ScaleBytes);
+    mbar_arrive_expect_tx(&bar_w, bytes);
+    bulk_g2s(sw, p.wimg, bytes, &bar_w);
+  }
+  const uint32_t lane_base = uint32_t((warp & 3) * 32) << 16;
+  SlotTmem st;
+  st.tmem = tmem;
+  st.acc_col = uint32_t(slot * kSlotCols);
+  st.act_col = st.acc_col + 64;
+  st.t_acc = tmem + lane_base + st.acc_col;
+  st.t_act = tmem + lane_base + st.act_col;
+  const uint32_t sw_base = smem_u32(sw);
+  const int64_t n_tiles = (p.n + kTile - 1) / kTile;
+  const int64_t stride = int64_t(gridDim.x) * kSlots;
+  RecStage rs;
+  rs.row0 = smem_u32(recs) + uint32_t(slot * 2 * 8192 + rit * 64);
+  rs.p = recs + slot * 2 * 8192 + rit * 64;
+  rs.rot = uint32_t((rit >> 1) & 3);
+  auto prefetch = [&](int64_t t, int b) {
+    const int64_t row = t * kTile + rit;
+    rs.fetch(p.rec, row, t < n_tiles && row < p.n, b);
+  };
+  int64_t tile = int64_t(blockIdx.x) * kSlots + slot;
+  int buf = 0;
+  prefetch(tile, buf);
+  mbar_wait(&bar_w, 0, p.err);
+  uint32_t phase = 0;
+  for (; tile < n_tiles; tile += stride) {
+    const int64_t row = tile * kTile + rit;
+    prefetch(tile + stride, buf ^ 1);
+    cp_async_wait<1>();
+    float r[kRecFloats];
+    rs.read(buf, r);
+    const uint8_t* fac_row = p.factor ? rs.p + buf * 8192 : nullptr;
+    buf ^= 1;
+    {  // encoded inputs times 128 (they lie in [-1, 1]) as E4M3
+      float f[kEncDims];
+      encode_record<MODE>(r, p.pad, f);
+      uint32_t pk[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        pk[j] = pack_e4m3x2<false>(f[4 * j] * 128.0f, f[4 * j + 1] * 128.0f) |
+                (pack_e4m3x2<false>(f[4 * j + 2] * 128.0f, f[4 * j + 3] * 128.0f) << 16);
+      tmem_st16(st.t_act, pk);
+      tmem_st_wait();
+    }
+    float inv_row = 1.0f / 128.0f;  // 1 / (the row's accumulated activation scale)
+    for (int l = 0; l < p.n_mats; ++l) {
+      fence_before();
+      named_sync(1 + slot, 128);
+      if (rit == 0) {
+        fence_after();
+        const uint32_t idesc = idesc_e4m3(128, p.img.rows[l]);
+        const uint32_t b0 = sw_base + uint32_t(img8_offset_of(p.img, l));
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+          mma_ts_f8(st.tmem + st.acc_col, st.tmem + st.act_col + uint32_t(k * 8), sdesc_sw64(b0 + uint32_t(k * 32), 512),
+                    idesc, k > 0 ? 1u : 0u);
+        mma_commit(&bar_mma[slot]);
+      }
+      if (rit == 0) mbar_wait(&bar_mma[slot], phase, p.err);
+      named_sync(1 + slot, 128);
+      phase ^= 1u;
+      fence_after();
+      inv_row *= inv_sw[l];  // the accumulator now carries the row scale times s_l
+      if (l + 1 < p.n_mats) {
+        uint32_t v[64], pk[16];
+        tmem_ld64(st.t_acc, v);
+        float amax = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 64; ++j) amax = fmaxf(amax, __uint_as_float(v[j]));
+        float c, inv_c;
+        pow2_scale(amax, c, inv_c);
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          pk[j] = pack_e4m3x2<true>(__uint_as_float(v[4 * j]) * c, __uint_as_float(v[4 * j + 1]) * c) |
+                  (pack_e4m3x2<true>(__uint_as_float(v[4 * j + 2]) * c, __uint_as_float(v[4 * j + 3]) * c) << 16);
+        tmem_st16(st.t_act, pk);
+        tmem_st_wait();
+        inv_row *= inv_c;
+      } else {
+        uint32_t v[4];
+        tmem_ld4(st.t_acc, v);
+        if (row < p.n) {
+          float y0 = __uint_as_float(v[0]) * inv_row, y1 = __uint_as_float(v[1]) * inv_row,
+                y2 = __uint_as_float(v[2]) * inv_row;
+          if (fac_row) {
+            float f[3];
+            staged_albedo_sum(fac_row, rs.rot, f);
+            y0 *= f[0];
+            y1 *= f[1];
+            y2 *= f[2];
+          }
+          float* o = p.rgb + row * 3;
+          o[0] = y0;
+          o[1] = y1;
+          o[2] = y2;
+        }
+      }
+    }
+  }
+  cp_async_wait<0>();
+  fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after();
+    tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
 // Raises a kernel's dynamic shared-memory limit once per process (the
 // attribute is per function; repeating the call on every launch costs
 // host time on the launch path).  `done` is per kernel instance.
@@ -923,4 +1119,49 @@ cudaError_t launch_train_batched(const Cache* proto, const TrainJob* jobs, int n
   return cudaGetLastError();
 }
 
+
+int img8_offset(const NetShape& net, int l) {
+  ImageShape img;
+  make_image_shape(net, &img);
+  return img8_offset_of(img, l);
+}
+
+cudaError_t launch_build_image_fp8(Cache* c, cudaStream_t st) {
+  const int bytes = img8_offset(c->net, c->net.n_mats);
+  cudaError_t e = cudaMemsetAsync(c->wimg8, 0, size_t(bytes), st);
+  if (e != cudaSuccess) return e;
+  k_build_image_fp8<<<c->net.n_mats, 256, 0, st>>>(query_weights(c), c->net, c->img, c->wimg8, bytes);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_infer_fp8(Cache* c, const float* rec, int64_t n, float* rgb, cudaStream_t st) {
+  InferParams p;
+  p.rec = rec;
+  p.n = n;
+  p.rgb = rgb;
+  p.wimg = c->wimg8;
+  p.img_bytes = img8_offset(c->net, c->net.n_mats);
+  p.n_mats = c->net.n_mats;
+  p.img = c->img;
+  p.pad = c->cfg.pad_value;
+  p.factor = c->cfg.refl_factor;
+  p.err = c->err;
+  const int img_alloc = (p.img_bytes + kImg8ScaleBytes + 1023) & ~1023;
+  const int smem = img_alloc + kSlots * 2 * 8192 + 1024;
+  const int64_t n_tiles = (n + kTile - 1) / kTile;
+  const int64_t want = (n_tiles + kSlots - 1) / kSlots;
+  const unsigned grid = unsigned(want < c->sm_count ? want : c->sm_count);
+  static int attr_done[2] = {0, 0};
+  cudaError_t e;
+  if (c->cfg.enc_mode == 0) {
+    e = set_smem(k_infer_fp8<0>, smem, &attr_done[0]);
+    if (e != cudaSuccess) return e;
+    k_infer_fp8<0><<<grid, kInferThreads, smem, st>>>(p);
+  } else {
+    e = set_smem(k_infer_fp8<1>, smem, &attr_done[1]);
+    if (e != cudaSuccess) return e;
+    k_infer_fp8<1><<<grid, kInferThreads, smem, st>>>(p);
+  }
+  return cudaGetLastError();
+}
 }  // namespace nrc

@@ -114,7 +114,7 @@ static nrc_status check_cfg(const nrc_config* cfg) {
   if (cfg->hidden_layers < 1 || cfg->hidden_layers > kMaxMats - 1)
     return set_error("hidden_layers must be in [1, %d]", kMaxMats - 1), NRC_ERR_INVALID_ARG;
   if (cfg->width != 64) return set_error("width %d unsupported (64 only)", cfg->width), NRC_ERR_UNSUPPORTED;
-  if (cfg->dtype < NRC_FP32 || cfg->dtype > NRC_BF16) return set_error("unknown dtype %d", cfg->dtype), NRC_ERR_INVALID_ARG;
+  if (cfg->dtype < NRC_FP32 || cfg->dtype > NRC_FP8) return set_error("unknown dtype %d", cfg->dtype), NRC_ERR_INVALID_ARG;
   if (cfg->enc_mode != NRC_ENC_CHEAP && cfg->enc_mode != NRC_ENC_EXACT)
     return set_error("unknown enc_mode %d", cfg->enc_mode), NRC_ERR_INVALID_ARG;
   if (cfg->loss_mode != NRC_LOSS_LUMINANCE && cfg->loss_mode != NRC_LOSS_PER_CHANNEL)
@@ -216,6 +216,7 @@ static void free_cache(nrc_cache* c) {
   cudaFree(c->wimg);
   cudaFree(c->ema);
   cudaFree(c->wimg_ema);
+  cudaFree(c->wimg8);
   cudaFree(c->sh_g);
   cudaFree(c->sh_stats);
   cudaFree(c->sh_roots);
@@ -257,6 +258,8 @@ nrc_status nrc_create(const nrc_config* cfg, nrc_stream stream, nrc_cache** out)
   if (e == cudaSuccess) e = cudaMalloc(&c->wimg, size_t(c->img.off[c->net.n_mats]) + 1024);
   if (e == cudaSuccess) e = cudaMalloc(&c->err, sizeof(int));
   if (e == cudaSuccess && cfg->ema) e = cudaMalloc(&c->ema, np * 4);
+  if (e == cudaSuccess && cfg->dtype == NRC_FP8)
+    e = cudaMalloc(&c->wimg8, size_t(img8_offset(c->net, c->net.n_mats)) + kImg8ScaleBytes);
   if (e == cudaSuccess && cfg->ema) e = cudaMalloc(&c->wimg_ema, size_t(c->img.off[c->net.n_mats]) + 1024);
   const size_t sh_bytes = size_t(2 * c->net.n_mats) * kShampooStatFloats * 4;
   if (e == cudaSuccess && cfg->optimizer == NRC_OPT_SHAMPOO) e = cudaMalloc(&c->sh_g, np * 4);
@@ -323,6 +326,15 @@ static nrc_status infer_impl(nrc_cache* c, const float* rec, int64_t n, float* r
   cudaError_t e;
   if (c->cfg.path == NRC_PATH_PLAIN) {
     e = plain_infer(c, rec, n, rgb, st);
+  } else if (c->cfg.dtype == NRC_FP8) {
+    e = cudaSuccess;
+    if (c->wimg8_dirty) {
+      e = launch_build_image_fp8(c, st);
+      c->wimg8_dirty = false;
+      c->launches += 1;
+    }
+    if (e == cudaSuccess) e = launch_infer_fp8(c, rec, n, rgb, st);
+    c->launches += 1;
   } else if (c->cfg.dtype == NRC_FP32) {
     e = launch_infer_simt(c, rec, n, rgb, st);
     c->launches += 1;
@@ -360,6 +372,7 @@ nrc_status nrc_gather(const float* pool, const float* target, int64_t n_pool, in
 
 static nrc_status train_impl(nrc_cache* c, const float* pool, const float* target, int64_t n_pool, int64_t batch,
                              uint64_t frame_seed, int32_t step, float* loss_out, cudaStream_t st) {
+  c->wimg8_dirty = true;
   uint64_t a, cc;
   lcg_params(n_pool, frame_seed, &a, &cc);
   cudaError_t e;
@@ -488,6 +501,7 @@ nrc_status nrc_set_state(nrc_cache* c, const float* w, const float* m, const flo
   if (e == cudaSuccess) e = reset_ema(c, st);
   if (e == cudaSuccess) e = reset_shampoo(c, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  c->wimg8_dirty = true;
   return cuda_status(e, "nrc_set_state");
 }
 
@@ -507,6 +521,7 @@ nrc_status nrc_set_ema(nrc_cache* c, const float* ema, nrc_stream stream) {
   cudaError_t e = cudaMemcpyAsync(c->ema, ema, size_t(c->net.n_params) * 4, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && c->cfg.dtype != NRC_FP32) e = launch_build_image_of(c, c->ema, c->wimg_ema, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  c->wimg8_dirty = true;
   return cuda_status(e, "nrc_set_ema");
 }
 

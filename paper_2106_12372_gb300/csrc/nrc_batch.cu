@@ -32,7 +32,7 @@ bool batch_same_cfg(const nrc_config& a, const nrc_config& b) {
 nrc_status batch_check(nrc_cache* const* caches, int n_caches) {
   for (int c = 0; c < n_caches; ++c) {
     if (!caches[c]) return set_error("batched caches: cache %d is NULL", c), NRC_ERR_INVALID_ARG;
-    if (caches[c]->cfg.dtype == NRC_FP32)
+    if (caches[c]->cfg.dtype != NRC_FP16 && caches[c]->cfg.dtype != NRC_BF16)
       return set_error("batched caches compute in FP16 or BF16"), NRC_ERR_UNSUPPORTED;
     if (caches[c]->cfg.optimizer != NRC_OPT_ADAM)
       return set_error("batched caches train with Adam"), NRC_ERR_UNSUPPORTED;

@@ -57,6 +57,8 @@ struct Cache {
   float* v = nullptr;     // Adam second moment
   long long* t = nullptr; // Adam step counter (device)
   uint8_t* wimg = nullptr;        // 16-bit weight image (tensor-core path)
+  uint8_t* wimg8 = nullptr;       // E4M3 image of the queried weights (NRC_FP8), + per-layer 1/scale
+  bool wimg8_dirty = true;        // the weights changed since wimg8 was built
   float* ema = nullptr;           // weight average of Eq. 2 (cfg.ema), FP32 [n_params]
   uint8_t* wimg_ema = nullptr;    // its 16-bit image (what queries read when cfg.ema)
   // Shampoo (cfg.optimizer): gradient, statistics L_l/R_l and their inverse
@@ -158,6 +160,13 @@ inline const float* query_weights(const Cache* c) { return c->cfg.ema ? c->ema :
 inline const uint8_t* query_image(const Cache* c) { return c->cfg.ema ? c->wimg_ema : c->wimg; }
 cudaError_t launch_step_increment(Cache* c, cudaStream_t st);
 cudaError_t launch_infer_tc(Cache* c, const float* rec, int64_t n, float* rgb, cudaStream_t st);
+// E4M3 image (64-byte swizzle, matrix l at img8_offset(net, l)) of the queried
+// weights with its per-layer 1/scale floats after the last matrix.
+int img8_offset(const NetShape& net, int l);
+constexpr int kImg8ScaleBytes = 32;  // per-layer 1/scale floats (kMaxMats used), a multiple of 16 bytes
+cudaError_t launch_build_image_fp8(Cache* c, cudaStream_t st);
+cudaError_t launch_infer_fp8(Cache* c, const float* rec, int64_t n, float* rgb, cudaStream_t st);
+inline bool fp16_like(int dtype) { return dtype == NRC_FP16 || dtype == NRC_FP8; }
 // One persistent launch over the units of several caches (device arrays);
 // proto supplies the shape, dtype and encoding shared by all of them.
 cudaError_t launch_infer_batched(const Cache* proto, const BatchCache* caches, const BatchUnit* units, int n_units,

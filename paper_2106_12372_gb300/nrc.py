@@ -19,12 +19,12 @@ LIB_PATH = os.path.join(HERE, "libnrc.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "nrc.h")
 
 NRC_OK, NRC_ERR_INVALID_ARG, NRC_ERR_CUDA, NRC_ERR_OOM, NRC_ERR_TIMEOUT, NRC_ERR_UNSUPPORTED, NRC_ERR_BUSY = range(7)
-FP32, FP16, BF16 = 0, 1, 2
+FP32, FP16, BF16, FP8 = 0, 1, 2, 3
 ENC_CHEAP, ENC_EXACT = 0, 1
 LOSS_LUMINANCE, LOSS_PER_CHANNEL = 0, 1
 PATH_FUSED, PATH_PLAIN = 0, 1
 OPT_ADAM, OPT_SHAMPOO = 0, 1
-DTYPES = {"fp32": FP32, "fp16": FP16, "bf16": BF16}
+DTYPES = {"fp32": FP32, "fp16": FP16, "bf16": BF16, "fp8": FP8}
 
 _lock = threading.Lock()
 _lib = None
