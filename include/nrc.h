@@ -100,7 +100,7 @@ enum {
 };
 
 typedef struct nrc_config {
-  int32_t width;         /* hidden width; 64 */
+  int32_t width;         /* hidden width; 64 (128: plain FP32 path only, the width-128 variant) */
   int32_t hidden_layers; /* number of hidden layers; 5 (1..8) */
   int32_t dtype;         /* NRC_FP32 | NRC_FP16 | NRC_BF16 */
   int32_t enc_mode;      /* NRC_ENC_CHEAP | NRC_ENC_EXACT */

@@ -113,7 +113,10 @@ static nrc_status check_cfg(const nrc_config* cfg) {
   if (!cfg) return set_error("cfg is NULL"), NRC_ERR_INVALID_ARG;
   if (cfg->hidden_layers < 1 || cfg->hidden_layers > kMaxMats - 1)
     return set_error("hidden_layers must be in [1, %d]", kMaxMats - 1), NRC_ERR_INVALID_ARG;
-  if (cfg->width != 64) return set_error("width %d unsupported (64 only)", cfg->width), NRC_ERR_UNSUPPORTED;
+  if (cfg->width != 64 && cfg->width != 128) return set_error("width %d unsupported (64 or 128)", cfg->width), NRC_ERR_UNSUPPORTED;
+  if (cfg->width != 64 && (cfg->dtype != NRC_FP32 || cfg->path != NRC_PATH_PLAIN || cfg->optimizer != NRC_OPT_ADAM))
+    return set_error("width 128 runs on the plain FP32 path with Adam only (dtype NRC_FP32, path NRC_PATH_PLAIN)"),
+           NRC_ERR_UNSUPPORTED;
   if (cfg->dtype < NRC_FP32 || cfg->dtype > NRC_FP8) return set_error("unknown dtype %d", cfg->dtype), NRC_ERR_INVALID_ARG;
   if (cfg->enc_mode != NRC_ENC_CHEAP && cfg->enc_mode != NRC_ENC_EXACT)
     return set_error("unknown enc_mode %d", cfg->enc_mode), NRC_ERR_INVALID_ARG;
@@ -304,6 +307,8 @@ nrc_status nrc_destroy(nrc_cache* c) {
 nrc_status nrc_set_path(nrc_cache* c, int32_t path) {
   if (!c) return set_error("cache is NULL"), NRC_ERR_INVALID_ARG;
   if (path != NRC_PATH_FUSED && path != NRC_PATH_PLAIN) return set_error("unknown path %d", path), NRC_ERR_INVALID_ARG;
+  if (path == NRC_PATH_FUSED && c->cfg.width != 64)
+    return set_error("the fused kernels take width 64 only"), NRC_ERR_UNSUPPORTED;
   c->cfg.path = path;
   return NRC_OK;
 }

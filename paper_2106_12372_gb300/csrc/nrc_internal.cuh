@@ -163,7 +163,7 @@ cudaError_t launch_infer_tc(Cache* c, const float* rec, int64_t n, float* rgb, c
 // E4M3 image (64-byte swizzle, matrix l at img8_offset(net, l)) of the queried
 // weights with its per-layer 1/scale floats after the last matrix.
 int img8_offset(const NetShape& net, int l);
-constexpr int kImg8ScaleBytes = 32;  // per-layer 1/scale floats (kMaxMats used), a multiple of 16 bytes
+constexpr int kImg8ScaleBytes = 48;  // per-layer 1/scale floats (kMaxMats of 12), a multiple of 16 bytes
 cudaError_t launch_build_image_fp8(Cache* c, cudaStream_t st);
 cudaError_t launch_infer_fp8(Cache* c, const float* rec, int64_t n, float* rgb, cudaStream_t st);
 inline bool fp16_like(int dtype) { return dtype == NRC_FP16 || dtype == NRC_FP8; }
