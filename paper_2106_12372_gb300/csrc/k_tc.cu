@@ -555,12 +555,12 @@ static cudaError_t set_smem(K kernel, int bytes, int* done) {
   return e;
 }
 
-cudaError_t launch_infer_tc(Cache* c, const float* rec, int64_t n, float* rgb, cudaStream_t st) {
+cudaError_t launch_infer_tc(Cache* c, const float* rec, int64_t n, float* rgb, cudaStream_t st, const uint8_t* image) {
   InferParams p;
   p.rec = rec;
   p.n = n;
   p.rgb = rgb;
-  p.wimg = query_image(c);
+  p.wimg = image ? image : query_image(c);
   p.img_bytes = c->img.off[c->net.n_mats];
   p.n_mats = c->net.n_mats;
   p.img = c->img;

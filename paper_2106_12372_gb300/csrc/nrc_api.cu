@@ -1,5 +1,6 @@
 // C ABI of the neural radiance cache library (include/nrc.h): argument
 // checking, cache state ownership, and the launch sequences of each call.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -228,6 +229,12 @@ static void free_cache(nrc_cache* c) {
   cudaFree(c->err);
   cudaFree(c->plain_buf);
   cudaFree(c->stage);
+  cudaFree(c->wimg_snap);
+  for (cudaEvent_t e : c->ev_pipe)
+    if (e) cudaEventDestroy(e);
+  if (c->s_h2d) cudaStreamDestroy(c->s_h2d);
+  if (c->s_query) cudaStreamDestroy(c->s_query);
+  if (c->s_d2h) cudaStreamDestroy(c->s_d2h);
   delete c;
 }
 
@@ -434,6 +441,75 @@ nrc_status nrc_frame(nrc_cache* c, const float* queries, int64_t n_q, float* rgb
   return NRC_OK;
 }
 
+namespace nrc {
+// nrc_frame_host for the tensor-core path, pipelined: the queries go up in
+// chunks on s_h2d, each chunk is answered on s_query as soon as it has landed
+// and comes back on s_d2h, while the frame's training steps run on the
+// caller's stream against the pool (uploaded first).  The queries read a
+// snapshot of the starting weight image, so that they see the weights from
+// before the frame's training, as the sequential frame does.
+constexpr int kPipeChunks = 8;
+static nrc_status frame_host_pipelined(nrc_cache* c, const float* queries, int64_t n_q, float* rgb, const float* pool,
+                                       const float* target, int64_t n_pool, int64_t batch, int32_t n_steps,
+                                       uint64_t frame_seed, float* loss_out, float* dq, float* dr, float* dp, float* dt,
+                                       float* dl, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  if (!c->s_h2d) {
+    e = cudaStreamCreateWithFlags(&c->s_h2d, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->s_query, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->s_d2h, cudaStreamNonBlocking);
+    for (int i = 0; i < 20 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&c->ev_pipe[i], cudaEventDisableTiming);
+    const size_t img_bytes = size_t(c->img.off[c->net.n_mats]) + 1024;
+    if (e == cudaSuccess) e = cudaMalloc(&c->wimg_snap, img_bytes);
+    if (e != cudaSuccess) return cuda_status(e, "nrc_frame_host pipeline set-up");
+  }
+  cudaEvent_t ev_start = c->ev_pipe[0], ev_snap = c->ev_pipe[1], ev_pool = c->ev_pipe[2], ev_train = c->ev_pipe[3];
+  cudaEvent_t* ev_h = c->ev_pipe + 4;
+  cudaEvent_t* ev_q = c->ev_pipe + 12;
+  // the caller's earlier work, then the weight snapshot (stream order on st)
+  e = cudaEventRecord(ev_start, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->wimg_snap, query_image(c), size_t(c->img.off[c->net.n_mats]), cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaEventRecord(ev_snap, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->s_h2d, ev_start, 0);
+  if (e == cudaSuccess && n_pool > 0 && pool) e = cudaMemcpyAsync(dp, pool, size_t(n_pool) * 64, cudaMemcpyHostToDevice, c->s_h2d);
+  if (e == cudaSuccess && n_pool > 0 && target)
+    e = cudaMemcpyAsync(dt, target, size_t(n_pool) * 12, cudaMemcpyHostToDevice, c->s_h2d);
+  if (e == cudaSuccess) e = cudaEventRecord(ev_pool, c->s_h2d);
+  // training on the caller's stream once the pool is up
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev_pool, 0);
+  if (e != cudaSuccess) return cuda_status(e, "nrc_frame_host");
+  if (n_steps > 0 && batch > 0) {
+    nrc_status s = nrc_frame(c, dq, 0, dr, dp, dt, n_pool, batch, n_steps, frame_seed, loss_out ? dl : nullptr,
+                             reinterpret_cast<nrc_stream>(st));
+    if (s != NRC_OK) return s;
+  }
+  e = cudaEventRecord(ev_train, st);
+  // queries in chunks of whole 128-row tiles
+  const int64_t tiles = (n_q + kTile - 1) / kTile;
+  const int chunks = int(std::min<int64_t>(kPipeChunks, std::max<int64_t>(1, tiles / 512)));
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->s_query, ev_snap, 0);
+  for (int k = 0; k < chunks && e == cudaSuccess; ++k) {
+    const int64_t b = tiles * k / chunks * kTile, en = std::min<int64_t>(n_q, tiles * (k + 1) / chunks * kTile);
+    if (en <= b) continue;
+    cudaStream_t hs = c->s_h2d;
+    e = cudaMemcpyAsync(dq + b * 16, queries + b * 16, size_t(en - b) * 64, cudaMemcpyHostToDevice, hs);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_h[k], hs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->s_query, ev_h[k], 0);
+    if (e == cudaSuccess) e = launch_infer_tc(c, dq + b * 16, en - b, dr + b * 3, c->s_query, c->wimg_snap);
+    c->launches += 1;
+    if (e == cudaSuccess) e = cudaEventRecord(ev_q[k], c->s_query);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->s_d2h, ev_q[k], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(rgb + b * 3, dr + b * 3, size_t(en - b) * 12, cudaMemcpyDeviceToHost, c->s_d2h);
+  }
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->s_d2h, ev_train, 0);
+  if (e == cudaSuccess && loss_out && n_steps > 0)
+    e = cudaMemcpyAsync(loss_out, dl, size_t(n_steps) * 4, cudaMemcpyDeviceToHost, c->s_d2h);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->s_d2h);
+  return cuda_status(e, "nrc_frame_host");
+}
+}  // namespace nrc
+
 nrc_status nrc_frame_host(nrc_cache* c, const float* queries, int64_t n_q, float* rgb, const float* pool,
                           const float* target, int64_t n_pool, int64_t batch, int32_t n_steps, uint64_t frame_seed,
                           float* loss_out, nrc_stream stream) {
@@ -461,6 +537,9 @@ nrc_status nrc_frame_host(nrc_cache* c, const float* queries, int64_t n_q, float
   float* dt = reinterpret_cast<float*>(base + bq + br + bp);
   float* dl = reinterpret_cast<float*>(base + bq + br + bp + bt);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (n_q > 0 && c->cfg.path == NRC_PATH_FUSED && (c->cfg.dtype == NRC_FP16 || c->cfg.dtype == NRC_BF16))
+    return frame_host_pipelined(c, queries, n_q, rgb, pool, target, n_pool, batch, n_steps, frame_seed, loss_out, dq, dr,
+                                dp, dt, dl, st);
   cudaError_t e = cudaSuccess;
   if (n_q > 0) e = cudaMemcpyAsync(dq, queries, size_t(n_q) * 64, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && n_pool > 0 && pool) e = cudaMemcpyAsync(dp, pool, size_t(n_pool) * 64, cudaMemcpyHostToDevice, st);

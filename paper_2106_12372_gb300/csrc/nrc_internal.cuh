@@ -76,6 +76,11 @@ struct Cache {
   // nrc_frame_host staging (grown on demand)
   void* stage = nullptr;
   size_t stage_bytes = 0;
+  // nrc_frame_host pipeline (created on first use): query uploads, queries and
+  // read-backs on their own streams, the queries on a snapshot of the image
+  cudaStream_t s_h2d = nullptr, s_query = nullptr, s_d2h = nullptr;
+  cudaEvent_t ev_pipe[20] = {};
+  uint8_t* wimg_snap = nullptr;
   long long launches = 0;
   int sm_count = 0;
   int device = 0;
@@ -159,7 +164,9 @@ cudaError_t launch_build_image_of(const Cache* c, const float* w, uint8_t* img, 
 inline const float* query_weights(const Cache* c) { return c->cfg.ema ? c->ema : c->w; }
 inline const uint8_t* query_image(const Cache* c) { return c->cfg.ema ? c->wimg_ema : c->wimg; }
 cudaError_t launch_step_increment(Cache* c, cudaStream_t st);
-cudaError_t launch_infer_tc(Cache* c, const float* rec, int64_t n, float* rgb, cudaStream_t st);
+// image: the weight image to read (nullptr: the cache's queried image)
+cudaError_t launch_infer_tc(Cache* c, const float* rec, int64_t n, float* rgb, cudaStream_t st,
+                            const uint8_t* image = nullptr);
 // E4M3 image (64-byte swizzle, matrix l at img8_offset(net, l)) of the queried
 // weights with its per-layer 1/scale floats after the last matrix.
 int img8_offset(const NetShape& net, int l);
