@@ -486,12 +486,17 @@ NRC_API nrc_status nrc_paths_terminate(const nrc_paths* paths, const nrc_path_pa
                                        float* render_queries, float* render_emitted, float* render_throughput,
                                        int32_t* tiles, float* tail_queries, nrc_stream stream);
 
+/* Length of the offsets scratch nrc_paths_records needs for n_tiles training
+ * tiles: n_tiles entries plus one per 2048 tiles (the scan's block totals). */
+NRC_API int64_t nrc_paths_offsets_count(int64_t n_tiles);
+
 /* Self-training records (Sec. 3.3): for each training path, in tile order, the
  * records of x_0 .. x_{m-1} with targets L_j = w_j (Le_{j+1} + L_{j+1}) from
  * L_m = tail_rgb[t] (the cache's value at x_m; 0 where the roulette ended an
  * unbiased suffix).  Writes min(total, max_records) records into pool
- * [max][16] and targets [max][3]; offsets [n_tiles] (device int64 scratch)
- * receives each path's first record, *count (device int64) the total. */
+ * [max][16] and targets [max][3]; offsets (device int64 scratch of
+ * nrc_paths_offsets_count(n_tiles) entries) receives in its first n_tiles
+ * entries each path's first record, *count (device int64) the total. */
 NRC_API nrc_status nrc_paths_records(const nrc_paths* paths, const nrc_path_params* params, const int32_t* tiles,
                                      const float* tail_rgb, float* pool, float* targets, int64_t max_records,
                                      int64_t* offsets, int64_t* count, nrc_stream stream);

@@ -474,9 +474,10 @@ __global__ void __launch_bounds__(kInferThreads, 1) k_infer_fp8(const __grid_con
       encode_record<MODE>(r, p.pad, f);
       uint32_t pk[16];
 #pragma unroll
+      for (int j = 0; j < kEncDims; j += 2) mul2(f[j], f[j + 1], 128.0f);
+#pragma unroll
       for (int j = 0; j < 16; ++j)
-        pk[j] = pack_e4m3x2<false>(f[4 * j] * 128.0f, f[4 * j + 1] * 128.0f) |
-                (pack_e4m3x2<false>(f[4 * j + 2] * 128.0f, f[4 * j + 3] * 128.0f) << 16);
+        pk[j] = pack_e4m3x2<false>(f[4 * j], f[4 * j + 1]) | (pack_e4m3x2<false>(f[4 * j + 2], f[4 * j + 3]) << 16);
       tmem_st16(st.t_act, pk);
       tmem_st_wait();
     }
@@ -502,15 +503,25 @@ __global__ void __launch_bounds__(kInferThreads, 1) k_infer_fp8(const __grid_con
       if (l + 1 < p.n_mats) {
         uint32_t v[64], pk[16];
         tmem_ld64(st.t_acc, v);
-        float amax = 0.0f;
+        float x[64];
 #pragma unroll
-        for (int j = 0; j < 64; ++j) amax = fmaxf(amax, __uint_as_float(v[j]));
+        for (int j = 0; j < 64; ++j) x[j] = __uint_as_float(v[j]);
+        // the row's amax (of the ReLU'd values) by a tree of three-input maxima
+        float m[22], q[8];
+#pragma unroll
+        for (int j = 0; j < 21; ++j) m[j] = max3(x[3 * j], x[3 * j + 1], x[3 * j + 2]);
+        m[21] = fmaxf(x[63], 0.0f);
+#pragma unroll
+        for (int j = 0; j < 7; ++j) q[j] = max3(m[3 * j], m[3 * j + 1], m[3 * j + 2]);
+        q[7] = m[21];
+        const float amax = max3(max3(q[0], q[1], q[2]), max3(q[3], q[4], q[5]), fmaxf(q[6], q[7]));
         float c, inv_c;
         pow2_scale(amax, c, inv_c);
 #pragma unroll
+        for (int j = 0; j < 64; j += 2) mul2(x[j], x[j + 1], c);
+#pragma unroll
         for (int j = 0; j < 16; ++j)
-          pk[j] = pack_e4m3x2<true>(__uint_as_float(v[4 * j]) * c, __uint_as_float(v[4 * j + 1]) * c) |
-                  (pack_e4m3x2<true>(__uint_as_float(v[4 * j + 2]) * c, __uint_as_float(v[4 * j + 3]) * c) << 16);
+          pk[j] = pack_e4m3x2<true>(x[4 * j], x[4 * j + 1]) | (pack_e4m3x2<true>(x[4 * j + 2], x[4 * j + 3]) << 16);
         tmem_st16(st.t_act, pk);
         tmem_st_wait();
         inv_row *= inv_c;

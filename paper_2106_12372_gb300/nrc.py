@@ -144,6 +144,7 @@ def lib() -> ctypes.CDLL:
             "nrc_get_ema": (i32, [P, P, P]),
             "nrc_paths_tile_count": (i64, [i32, i32, i32]),
             "nrc_paths_adapt_tile": (i32, [i32, i64, i64]),
+            "nrc_paths_offsets_count": (i64, [i64]),
             "nrc_paths_terminate": (i32, [P, P, P, P, P, P, P, P]),
             "nrc_paths_records": (i32, [P, P, P, P, P, P, i64, P, P, P]),
             "nrc_paths_composite": (i32, [P, P, P, i64, P, P]),
@@ -502,6 +503,10 @@ def paths_tile_count(width: int, height: int, tile: int) -> int:
     return lib().nrc_paths_tile_count(width, height, tile)
 
 
+def paths_offsets_count(n_tiles: int) -> int:
+    return lib().nrc_paths_offsets_count(n_tiles)
+
+
 def paths_adapt_tile(tile: int, generated: int, target: int) -> int:
     return lib().nrc_paths_adapt_tile(tile, generated, target)
 
@@ -510,18 +515,21 @@ def _paths(vertices, width, height, camera):
     return _Paths(_ptr(vertices), width, height, vertices.shape[1], (ctypes.c_float * 3)(*camera))
 
 
-def paths_terminate(vertices, width: int, height: int, camera, params: PathParams, stream=None):
-    """(render_queries, render_emitted, render_throughput, tiles, tail_queries) as device tensors."""
+def paths_terminate(vertices, width: int, height: int, camera, params: PathParams, stream=None, out=None):
+    """(render_queries, render_emitted, render_throughput, tiles, tail_queries) as device tensors;
+    `out` may hold these five tensors, preallocated (the tail queries of tiles without a
+    training pixel are left as they are, so zero them once)."""
     import torch
 
     d = vertices.device
     P = width * height
     nt = paths_tile_count(width, height, params.tile)
-    rq = torch.empty((P, 16), device=d)
-    em = torch.empty((P, 3), device=d)
-    tp = torch.empty((P, 3), device=d)
-    tiles = torch.empty((nt, 4), dtype=torch.int32, device=d)
-    tq = torch.zeros((nt, 16), device=d)
+    if out is None:
+        out = (torch.empty((P, 16), device=d), torch.empty((P, 3), device=d), torch.empty((P, 3), device=d),
+               torch.empty((nt, 4), dtype=torch.int32, device=d), torch.zeros((nt, 16), device=d))
+    rq, em, tp, tiles, tq = out
+    if rq.shape[0] < P or em.shape[0] < P or tp.shape[0] < P or tiles.shape[0] < nt or tq.shape[0] < nt:
+        raise ValueError("paths_terminate: output tensors too small")
     ps = _paths(vertices, width, height, camera)
     _check(lib().nrc_paths_terminate(ctypes.byref(ps), ctypes.byref(params), _ptr(rq), _ptr(em), _ptr(tp),
                                      _ptr(tiles), _ptr(tq), _stream(stream)))
@@ -529,25 +537,30 @@ def paths_terminate(vertices, width: int, height: int, camera, params: PathParam
 
 
 def paths_records(vertices, width: int, height: int, camera, params: PathParams, tiles, tail_rgb, max_records: int,
-                  stream=None):
-    """(pool [max,16], targets [max,3], count device int64 [1])."""
+                  stream=None, out=None):
+    """(pool [max,16], targets [max,3], count device int64 [1]); `out` may hold
+    (pool, targets, offsets [paths_offsets_count(n_tiles)] int64, count [1] int64), preallocated."""
     import torch
 
     d = vertices.device
-    pool = torch.zeros((max_records, 16), device=d)
-    tg = torch.zeros((max_records, 3), device=d)
-    offsets = torch.empty(tiles.shape[0], dtype=torch.int64, device=d)
-    count = torch.zeros(1, dtype=torch.int64, device=d)
+    if out is None:
+        out = (torch.zeros((max_records, 16), device=d), torch.zeros((max_records, 3), device=d),
+               torch.empty(paths_offsets_count(tiles.shape[0]), dtype=torch.int64, device=d),
+               torch.zeros(1, dtype=torch.int64, device=d))
+    pool, tg, offsets, count = out
+    if (pool.shape[0] < max_records or tg.shape[0] < max_records
+            or offsets.shape[0] < paths_offsets_count(tiles.shape[0])):
+        raise ValueError("paths_records: output tensors too small")
     ps = _paths(vertices, width, height, camera)
     _check(lib().nrc_paths_records(ctypes.byref(ps), ctypes.byref(params), _ptr(tiles), _ptr(tail_rgb), _ptr(pool),
                                    _ptr(tg), max_records, _ptr(offsets), _ptr(count), _stream(stream)))
     return pool, tg, count
 
 
-def paths_composite(emitted, throughput, rgb, stream=None):
+def paths_composite(emitted, throughput, rgb, stream=None, out=None):
     import torch
 
-    img = torch.empty_like(emitted)
+    img = torch.empty_like(emitted) if out is None else out
     _check(lib().nrc_paths_composite(_ptr(emitted), _ptr(throughput), _ptr(rgb), emitted.shape[0], _ptr(img),
                                      _stream(stream)))
     return img

@@ -2,6 +2,12 @@
 
     python -m paper_2106_12372_gb300.profile_case --what infer --n 2073600 --dtype fp16 --iters 3
     python -m paper_2106_12372_gb300.profile_case --what train --batch 16384 --dtype fp16 --iters 3
+    python -m paper_2106_12372_gb300.profile_case --what paths --width 1920 --height 1080 --iters 3
+
+``paths`` runs the training-record pipeline around the query (terminate, the
+render and tail queries, the self-training records, 4 training steps, the
+composite) on synthetic 10-vertex paths: a quarter-resolution path set tiled
+4 x 4 over the frame, training tiles of 8 x 8 pixels.
 """
 from __future__ import annotations
 
@@ -14,7 +20,9 @@ from paper_2106_12372_gb300 import build, nrc, synth
 
 def main() -> None:
     ap = argparse.ArgumentParser()
-    ap.add_argument("--what", choices=["infer", "train", "frame"], default="infer")
+    ap.add_argument("--what", choices=["infer", "train", "frame", "paths"], default="infer")
+    ap.add_argument("--width", type=int, default=1920)
+    ap.add_argument("--height", type=int, default=1080)
     ap.add_argument("--n", type=int, default=1920 * 1080)
     ap.add_argument("--batch", type=int, default=16384)
     ap.add_argument("--steps", type=int, default=4)
@@ -23,6 +31,9 @@ def main() -> None:
     args = ap.parse_args()
     build.build()
     dev = torch.device("cuda:0")
+    if args.what == "paths":
+        run_paths(args, dev)
+        return
     cache = nrc.Cache(dtype=args.dtype)
     pool_np, tgt_np = synth.make_training_pool(args.batch * args.steps, seed=5)
     pool, tgt = torch.from_numpy(pool_np).to(dev), torch.from_numpy(tgt_np).to(dev)
@@ -34,6 +45,28 @@ def main() -> None:
         if args.what in ("train", "frame"):
             for s in range(args.steps):
                 cache.train_step(pool, tgt, args.batch, synth.frame_seed(5, it), s)
+    torch.cuda.synchronize()
+    cache.check_error()
+    print("ok")
+
+
+def run_paths(args, dev) -> None:
+    W, H, K, rep = args.width, args.height, 10, 4
+    if W % rep or H % rep:
+        raise SystemExit("--width and --height must be multiples of 4")
+    v = torch.from_numpy(synth.make_paths(W // rep, H // rep, K, seed=2109)).to(dev)
+    v = v.view(H // rep, W // rep, K, 24).repeat(rep, rep, 1, 1).reshape(W * H, K, 24).contiguous()
+    cache = nrc.Cache(dtype=args.dtype)
+    cam = synth.PATH_CAMERA
+    rgb = torch.empty((W * H, 3), device=dev)
+    for it in range(args.iters):
+        prm = nrc.PathParams(0.01, 8, it % 8, (3 * it) % 8, it % 16, 0.8)
+        rq, em, tp, tiles, tq = nrc.paths_terminate(v, W, H, cam, prm)
+        cache.infer(rq, rgb)
+        tail = cache.infer(tq)
+        pool, tg, count = nrc.paths_records(v, W, H, cam, prm, tiles, tail, args.batch * args.steps)
+        cache.frame(rq[:0], rgb[:0], pool, tg, args.batch, args.steps, synth.frame_seed(2109, it))
+        nrc.paths_composite(em, tp, rgb)
     torch.cuda.synchronize()
     cache.check_error()
     print("ok")

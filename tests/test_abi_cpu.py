@@ -75,3 +75,9 @@ def test_path_tiling_helpers_on_the_host():
     assert nrc.paths_adapt_tile(8, 65536 // 4, 65536) == 4
     assert nrc.paths_adapt_tile(8, 65536, 65536) == 8
     assert nrc.paths_adapt_tile(1, 1, 10 ** 9) == 1 and nrc.paths_adapt_tile(200, 10 ** 9, 1) == 256
+    # the records scan's scratch: the offsets plus one block total per 2048 tiles
+    assert nrc.paths_offsets_count(0) == 0
+    assert nrc.paths_offsets_count(1) == 2
+    assert nrc.paths_offsets_count(2048) == 2049
+    assert nrc.paths_offsets_count(2049) == 2051
+    assert nrc.paths_offsets_count(32400) == 32400 + 16

@@ -59,16 +59,19 @@ def test_termination_and_tiles_match_oracle(scene, c, tile, ox, oy, phase):
     assert (np.array(ref_tiles)[:, 0] >= 0).sum() > 10 and 0 < n.min() and n.max() <= K - 1
 
 
-def test_records_and_targets_match_oracle(scene):
+# tile 8: 104 tiles (one scan block); tile 1: every pixel trains, 5,917 tiles
+# (three scan blocks of 2,048, the last one ragged)
+@pytest.mark.parametrize("tile,ox,oy,phase,max_records", [(8, 3, 5, 7, 4096), (1, 0, 0, 5, 1 << 16)])
+def test_records_and_targets_match_oracle(scene, tile, ox, oy, phase, max_records):
     v, V = scene
-    prm = _params()
+    prm = _params(tile=tile, ox=ox, oy=oy, phase=phase)
     _, _, _, tiles, tq = nrc.paths_terminate(V, W, H, synth.PATH_CAMERA, prm)
-    _, _, _, ref_tiles = O.paths_terminate(v, W, H, synth.PATH_CAMERA, 0.01, 8, 3, 5, 7, 0.8)
+    _, _, _, ref_tiles = O.paths_terminate(v, W, H, synth.PATH_CAMERA, 0.01, tile, ox, oy, phase, 0.8)
     w0 = synth.xavier_weights(DIMS, seed=22)
     tail = O.infer(w0, DIMS, tq.cpu().numpy())  # the cache's values at the tails (FP64 oracle)
     ref_rec, ref_tg = O.paths_records(v, ref_tiles, tail, 0.8)
     pool, tg, count = nrc.paths_records(V, W, H, synth.PATH_CAMERA, prm, tiles,
-                                        torch.from_numpy(tail.astype(np.float32)).to(DEV), 4096)
+                                        torch.from_numpy(tail.astype(np.float32)).to(DEV), max_records)
     N = len(ref_rec)
     assert count.item() == N and N > 50
     assert np.array_equal(pool[:N].cpu().numpy().view(np.uint32), ref_rec.view(np.uint32))
@@ -108,3 +111,30 @@ def test_frame_through_the_cache(scene):
         assert torch.isfinite(img).all()
         tile = nrc.paths_adapt_tile(tile, n, 2048)
     cache.check_error()
+
+
+def test_preallocated_outputs_match(scene):
+    v, V = scene
+    prm = _params(tile=6, ox=2, oy=1, phase=3)
+    ref = nrc.paths_terminate(V, W, H, synth.PATH_CAMERA, prm)
+    nt = nrc.paths_tile_count(W, H, 6)
+    out = (torch.empty((W * H, 16), device=DEV), torch.empty((W * H, 3), device=DEV),
+           torch.empty((W * H, 3), device=DEV), torch.empty((nt, 4), dtype=torch.int32, device=DEV),
+           torch.zeros((nt, 16), device=DEV))
+    got = nrc.paths_terminate(V, W, H, synth.PATH_CAMERA, prm, out=out)
+    for a, b in zip(got, ref):
+        assert torch.equal(a, b)
+    tail = torch.rand((nt, 3), device=DEV, generator=torch.Generator(device=DEV).manual_seed(5))
+    pr, tr, cr = nrc.paths_records(V, W, H, synth.PATH_CAMERA, prm, ref[3], tail, 4096)
+    bufs = (torch.full((4096, 16), 7.0, device=DEV), torch.full((4096, 3), 7.0, device=DEV),
+            torch.empty(nrc.paths_offsets_count(nt), dtype=torch.int64, device=DEV),
+            torch.zeros(1, dtype=torch.int64, device=DEV))
+    pg, tg_, cg = nrc.paths_records(V, W, H, synth.PATH_CAMERA, prm, ref[3], tail, 4096, out=bufs)
+    n = int(cr.item())
+    assert int(cg.item()) == n and 0 < n <= 4096
+    assert torch.equal(pg[:n], pr[:n]) and torch.equal(tg_[:n], tr[:n])
+    img = torch.empty((W * H, 3), device=DEV)
+    assert torch.equal(nrc.paths_composite(ref[1], ref[2], tail[:1].expand(W * H, 3).contiguous(), out=img),
+                       nrc.paths_composite(ref[1], ref[2], tail[:1].expand(W * H, 3).contiguous()))
+    with pytest.raises(ValueError):
+        nrc.paths_terminate(V, W, H, synth.PATH_CAMERA, prm, out=(out[0][:10],) + out[1:])
