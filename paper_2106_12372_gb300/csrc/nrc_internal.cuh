@@ -229,25 +229,87 @@ __device__ __forceinline__ void oneblob4(float s, float* out) {
   }
 }
 
+// Packed FP32 pairs: one instruction computes both lanes, each rounded exactly
+// as the scalar operation, so the paired code below gives the same bits as
+// its scalar form with half the arithmetic instructions.
+struct F2 {
+  float x, y;
+};
+__device__ __forceinline__ F2 fma_x2(F2 a, F2 b, F2 c) {
+  F2 d;
+  asm("{\n\t.reg .b64 a, b, c;\n\tmov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %5};\n\tmov.b64 c, {%6, %7};\n\t"
+      "fma.rn.f32x2 a, a, b, c;\n\tmov.b64 {%0, %1}, a;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+__device__ __forceinline__ F2 sub_x2(F2 a, F2 b) {
+  F2 d;
+  asm("{\n\t.reg .b64 a, b;\n\tmov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %5};\n\tsub.rn.f32x2 a, a, b;\n\t"
+      "mov.b64 {%0, %1}, a;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ F2 mul_x2(F2 a, F2 b) {
+  F2 d;
+  asm("{\n\t.reg .b64 a, b;\n\tmov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %5};\n\tmul.rn.f32x2 a, a, b;\n\t"
+      "mov.b64 {%0, %1}, a;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+
+// quartic_cdf of two arguments
+__device__ __forceinline__ F2 quartic_cdf_x2(F2 y) {
+  y.x = fminf(1.0f, fmaxf(-1.0f, y.x));
+  y.y = fminf(1.0f, fmaxf(-1.0f, y.y));
+  const F2 y2 = mul_x2(y, y);
+  return mul_x2(y, fma_x2(y2, fma_x2(y2, F2{0.1875f, 0.1875f}, F2{-0.625f, -0.625f}), F2{0.9375f, 0.9375f}));
+}
+
+// oneblob4<0> of two values side by side (a's bins to oa, b's to ob)
+__device__ __forceinline__ void oneblob4_quartic_x2(float a, float b, float* oa, float* ob) {
+  const F2 ks = mul_x2(F2{4.0f, 4.0f}, F2{a, b});
+  F2 prev = quartic_cdf_x2(F2{-ks.x, -ks.y});
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const F2 cur = quartic_cdf_x2(sub_x2(F2{float(i + 1), float(i + 1)}, ks));
+    const F2 m = sub_x2(cur, prev);
+    oa[i] = m.x;
+    ob[i] = m.y;
+    prev = cur;
+  }
+}
+
 template <int MODE>
 __device__ __forceinline__ void encode_record(const float* r, float pad, float* f) {
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
+    if (MODE == 0) {
+      // tri(2^d x - 1/2) = |4 frac(2^(d-1) x - 1/4) - 2| - 1; 2^(d-1) x is exact
+      const F2 xx{r[j], r[j]};
 #pragma unroll
-    for (int d = 0; d < 12; ++d) {
-      if (MODE == 0) {
-        // tri(2^d x - 1/2) = |4 frac(2^(d-1) x - 1/4) - 2| - 1; 2^(d-1) x is exact
-        const float t = fmaf(r[j], float(1 << d) * 0.5f, -0.25f);
-        f[12 * j + d] = fabsf(fmaf(4.0f, t - floorf(t), -2.0f)) - 1.0f;
-      } else {
-        f[12 * j + d] = sinpif(r[j] * float(1 << d));
+      for (int d = 0; d < 12; d += 2) {
+        const F2 t = fma_x2(xx, F2{float(1 << d) * 0.5f, float(2 << d) * 0.5f}, F2{-0.25f, -0.25f});
+        const F2 u = fma_x2(F2{4.0f, 4.0f}, sub_x2(t, F2{floorf(t.x), floorf(t.y)}), F2{-2.0f, -2.0f});
+        f[12 * j + d] = fabsf(u.x) - 1.0f;
+        f[12 * j + d + 1] = fabsf(u.y) - 1.0f;
       }
+    } else {
+#pragma unroll
+      for (int d = 0; d < 12; ++d) f[12 * j + d] = sinpif(r[j] * float(1 << d));
     }
   }
-  oneblob4<MODE>(r[3], f + 36);
-  oneblob4<MODE>(r[4], f + 40);
-  oneblob4<MODE>(r[5], f + 44);
-  oneblob4<MODE>(r[6], f + 48);
+  if (MODE == 0) {
+    oneblob4_quartic_x2(r[3], r[4], f + 36, f + 40);
+    oneblob4_quartic_x2(r[5], r[6], f + 44, f + 48);
+  } else {
+    oneblob4<MODE>(r[3], f + 36);
+    oneblob4<MODE>(r[4], f + 40);
+    oneblob4<MODE>(r[5], f + 44);
+    oneblob4<MODE>(r[6], f + 48);
+  }
   oneblob4<MODE>(-expm1f(-r[7]), f + 52);
 #pragma unroll
   for (int j = 0; j < 6; ++j) f[56 + j] = r[8 + j];

@@ -2,6 +2,9 @@
 (the precision sweep's wide variant) against the FP64 oracle: Xavier weights
 bit-identical, queries and one training step within 1e-5, and a 100-step loss
 curve that follows the oracle's pointwise over its first steps."""
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -75,11 +78,15 @@ def test_loss_curve_follows_the_oracle():
     ref = np.array(ref)
     print("width 128 curve: first 5", got[:5], ref[:5], "100-step medians", np.median(got), np.median(ref))
     # online training is chaotic: FP32 and FP64 runs agree step by step only at
-    # first; afterwards window medians of two faithful runs differ by up to 7 %
-    # over 100 steps (the loss-curve reading), so the whole run's median is held
-    # to 10 % (a 25-step window differed by 10 % in a faithful run)
+    # first; afterwards even FP64 runs whose initial weights differ by 1e-7
+    # drift apart (tests/golden/width128_curve_fp64.json: 100-step medians up to
+    # 17 % apart), so the GPU run's median is held to 1.5 x that spread around
+    # the oracle's (the loss-curve reading)
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "width128_curve_fp64.json")))
+    spread = max(abs(m - gold["medians"][0]) for m in gold["medians"][1:]) / gold["medians"][0]
+    print("oracle realizations' 100-step median spread", spread)
     assert np.all(np.abs(got[:20] - ref[:20]) <= 1e-2 * np.abs(ref[:20]))
-    assert abs(np.median(got) - np.median(ref)) <= 0.1 * np.median(ref)
+    assert abs(np.median(got) - np.median(ref)) <= max(0.05, 1.5 * spread) * np.median(ref)
     c.check_error()
 
 
