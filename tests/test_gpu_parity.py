@@ -238,24 +238,28 @@ def test_frame_equals_separate_calls():
     assert np.array_equal(a.get_state()[0], b.get_state()[0])
 
 
-def test_frame_host_equals_frame():
+# 5,000 queries: one chunk; 300,001: the pipelined path's 4 chunks of whole tiles, the last one ragged
+@pytest.mark.parametrize("n_q", [5000, 300_001])
+def test_frame_host_equals_frame(n_q):
     w0 = synth.xavier_weights(DIMS, seed=95)
-    qn = synth.make_records(5000, seed=96)
+    qn = synth.make_records(n_q, seed=96)
     pool, tgt = synth.make_training_pool(4096, seed=97)
     fs = synth.frame_seed(95, 0)
     a = nrc.Cache(dtype="fp16")
     a.set_state(w0)
     b = nrc.Cache(dtype="fp16")
     b.set_state(w0)
-    rgb_h = torch.empty((5000, 3)).pin_memory()
+    rgb_h = torch.empty((n_q, 3)).pin_memory()
     loss_h = torch.zeros(2).pin_memory()
     a.frame_host(torch.from_numpy(qn).pin_memory(), rgb_h, torch.from_numpy(pool).pin_memory(),
                  torch.from_numpy(tgt).pin_memory(), 1024, 2, fs, loss_out=loss_h)
-    rgb_d = torch.empty((5000, 3), device=DEV)
+    rgb_d = torch.empty((n_q, 3), device=DEV)
     loss_d = torch.zeros(2, device=DEV)
     b.frame(dev(qn), rgb_d, dev(pool), dev(tgt), 1024, 2, fs, loss_out=loss_d)
     torch.cuda.synchronize()
     assert torch.equal(rgb_h, rgb_d.cpu()) and torch.equal(loss_h, loss_d.cpu())
+    # the queries saw the weights from before the frame's training; both trained alike
+    assert np.array_equal(a.get_state()[0], b.get_state()[0])
 
 
 # -------------------------------------------------------------- plain path
