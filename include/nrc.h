@@ -506,6 +506,20 @@ NRC_API nrc_status nrc_paths_records(const nrc_paths* paths, const nrc_path_para
 NRC_API nrc_status nrc_paths_composite(const float* render_emitted, const float* render_throughput,
                                        const float* rgb, int64_t n, float* image, nrc_stream stream);
 
+/* Fault injection for tests (faults made on the host; nothing here
+ * faults the GPU).  nrc_debug_fail_device_allocs: after `after` more device
+ * allocations by this library (process-wide), the next `count` fail as if the
+ * device were out of memory; the call that needed them returns NRC_ERR_OOM and
+ * frees what it had allocated.  (0, 0) switches it off. */
+NRC_API void nrc_debug_fail_device_allocs(int32_t after, int32_t count);
+
+/* Runs, on `stream`, a one-thread kernel that waits through the library's
+ * bounded device wait on an mbarrier nothing arrives at, with a limit of
+ * limit_us microseconds (1 .. 2,000,000; the kernels use 2 s).  The wait gives
+ * up, sets the cache's error word and returns: the next nrc_check_error
+ * reports NRC_ERR_TIMEOUT and the cache stays usable. */
+NRC_API nrc_status nrc_debug_wait_timeout(nrc_cache* cache, int32_t limit_us, nrc_stream stream);
+
 /* Why the last failing call on this thread failed ("" if none). */
 NRC_API const char* nrc_last_error_string(void);
 

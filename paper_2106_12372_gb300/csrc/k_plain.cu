@@ -192,7 +192,7 @@ static cudaError_t ensure_plain(Cache* c, size_t bytes) {
   cudaFree(c->plain_buf);
   c->plain_buf = nullptr;
   c->plain_bytes = 0;
-  e = cudaMalloc(&c->plain_buf, bytes);
+  e = dev_alloc(&c->plain_buf, bytes);
   if (e == cudaSuccess) c->plain_bytes = bytes;
   return e;
 }

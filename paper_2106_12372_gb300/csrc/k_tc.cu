@@ -555,6 +555,23 @@ __global__ void __launch_bounds__(kInferThreads, 1) k_infer_fp8(const __grid_con
   }
 }
 
+// Fault-injection probe: one thread waits, through the kernels' bounded wait,
+// on an mbarrier that nothing arrives at; after limit_ns it sets kErrTimeout
+// in *err and the kernel returns (the context stays usable).
+__global__ void k_wait_probe(int* err, unsigned long long limit_ns) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_barrier_init();
+    mbar_wait(&bar, 0, err, limit_ns);
+  }
+}
+
+cudaError_t launch_wait_probe(int* err, unsigned long long limit_ns, cudaStream_t st) {
+  k_wait_probe<<<1, 32, 0, st>>>(err, limit_ns);
+  return cudaGetLastError();
+}
+
 // Raises a kernel's dynamic shared-memory limit once per process (the
 // attribute is per function; repeating the call on every launch costs
 // host time on the launch path).  `done` is per kernel instance.

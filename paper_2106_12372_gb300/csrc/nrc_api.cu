@@ -1,6 +1,7 @@
 // C ABI of the neural radiance cache library (include/nrc.h): argument
 // checking, cache state ownership, and the launch sequences of each call.
 #include <algorithm>
+#include <mutex>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -11,6 +12,24 @@
 #include "nrc_internal.cuh"
 
 namespace nrc {
+
+int g_alloc_skip = 0, g_alloc_fail = 0;
+static std::mutex g_alloc_mu;
+
+cudaError_t dev_alloc_bytes(void** p, size_t bytes) {
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    if (g_alloc_skip > 0) {
+      --g_alloc_skip;
+    } else if (g_alloc_fail > 0) {
+      --g_alloc_fail;
+      *p = nullptr;
+      return cudaErrorMemoryAllocation;
+    }
+  }
+  return cudaMalloc(p, bytes);
+}
+
 
 static thread_local char g_err[512] = "";
 
@@ -103,7 +122,7 @@ cudaError_t ensure_partials(Cache* c, int count) {
   cudaFree(c->partials);
   c->partials = nullptr;
   c->max_partials = 0;
-  e = cudaMalloc(&c->partials, size_t(count) * partial_stride(c->net.n_params) * 4);
+  e = dev_alloc(&c->partials, size_t(count) * partial_stride(c->net.n_params) * 4);
   if (e == cudaSuccess) c->max_partials = count;
   return e;
 }
@@ -261,21 +280,21 @@ nrc_status nrc_create(const nrc_config* cfg, nrc_stream stream, nrc_cache** out)
   }
   const size_t np = size_t(c->net.n_params);
   c->max_partials = 0;
-  if (e == cudaSuccess) e = cudaMalloc(&c->w, np * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&c->m, np * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&c->v, np * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&c->t, sizeof(long long));
-  if (e == cudaSuccess) e = cudaMalloc(&c->wimg, size_t(c->img.off[c->net.n_mats]) + 1024);
-  if (e == cudaSuccess) e = cudaMalloc(&c->err, sizeof(int));
-  if (e == cudaSuccess && cfg->ema) e = cudaMalloc(&c->ema, np * 4);
+  if (e == cudaSuccess) e = dev_alloc(&c->w, np * 4);
+  if (e == cudaSuccess) e = dev_alloc(&c->m, np * 4);
+  if (e == cudaSuccess) e = dev_alloc(&c->v, np * 4);
+  if (e == cudaSuccess) e = dev_alloc(&c->t, sizeof(long long));
+  if (e == cudaSuccess) e = dev_alloc(&c->wimg, size_t(c->img.off[c->net.n_mats]) + 1024);
+  if (e == cudaSuccess) e = dev_alloc(&c->err, sizeof(int));
+  if (e == cudaSuccess && cfg->ema) e = dev_alloc(&c->ema, np * 4);
   if (e == cudaSuccess && cfg->dtype == NRC_FP8)
-    e = cudaMalloc(&c->wimg8, size_t(img8_offset(c->net, c->net.n_mats)) + kImg8ScaleBytes);
-  if (e == cudaSuccess && cfg->ema) e = cudaMalloc(&c->wimg_ema, size_t(c->img.off[c->net.n_mats]) + 1024);
+    e = dev_alloc(&c->wimg8, size_t(img8_offset(c->net, c->net.n_mats)) + kImg8ScaleBytes);
+  if (e == cudaSuccess && cfg->ema) e = dev_alloc(&c->wimg_ema, size_t(c->img.off[c->net.n_mats]) + 1024);
   const size_t sh_bytes = size_t(2 * c->net.n_mats) * kShampooStatFloats * 4;
-  if (e == cudaSuccess && cfg->optimizer == NRC_OPT_SHAMPOO) e = cudaMalloc(&c->sh_g, np * 4);
-  if (e == cudaSuccess && cfg->optimizer == NRC_OPT_SHAMPOO) e = cudaMalloc(&c->sh_stats, sh_bytes);
-  if (e == cudaSuccess && cfg->optimizer == NRC_OPT_SHAMPOO) e = cudaMalloc(&c->sh_roots, sh_bytes);
-  if (e == cudaSuccess && cfg->optimizer == NRC_OPT_SHAMPOO) e = cudaMalloc(&c->sh_anorm, (np + 31) / 32 * 4);
+  if (e == cudaSuccess && cfg->optimizer == NRC_OPT_SHAMPOO) e = dev_alloc(&c->sh_g, np * 4);
+  if (e == cudaSuccess && cfg->optimizer == NRC_OPT_SHAMPOO) e = dev_alloc(&c->sh_stats, sh_bytes);
+  if (e == cudaSuccess && cfg->optimizer == NRC_OPT_SHAMPOO) e = dev_alloc(&c->sh_roots, sh_bytes);
+  if (e == cudaSuccess && cfg->optimizer == NRC_OPT_SHAMPOO) e = dev_alloc(&c->sh_anorm, (np + 31) / 32 * 4);
   if (e != cudaSuccess) {
     nrc_status st = cuda_status(e, "nrc_create allocation");
     free_cache(c);
@@ -454,13 +473,14 @@ static nrc_status frame_host_pipelined(nrc_cache* c, const float* queries, int64
                                        uint64_t frame_seed, float* loss_out, float* dq, float* dr, float* dp, float* dt,
                                        float* dl, cudaStream_t st) {
   cudaError_t e = cudaSuccess;
-  if (!c->s_h2d) {
-    e = cudaStreamCreateWithFlags(&c->s_h2d, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->s_query, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->s_d2h, cudaStreamNonBlocking);
-    for (int i = 0; i < 20 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&c->ev_pipe[i], cudaEventDisableTiming);
+  if (!c->wimg_snap) {  // set-up, resumable after a failure: each resource is made once
+    if (!c->s_h2d) e = cudaStreamCreateWithFlags(&c->s_h2d, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !c->s_query) e = cudaStreamCreateWithFlags(&c->s_query, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !c->s_d2h) e = cudaStreamCreateWithFlags(&c->s_d2h, cudaStreamNonBlocking);
+    for (int i = 0; i < 20 && e == cudaSuccess; ++i)
+      if (!c->ev_pipe[i]) e = cudaEventCreateWithFlags(&c->ev_pipe[i], cudaEventDisableTiming);
     const size_t img_bytes = size_t(c->img.off[c->net.n_mats]) + 1024;
-    if (e == cudaSuccess) e = cudaMalloc(&c->wimg_snap, img_bytes);
+    if (e == cudaSuccess) e = dev_alloc(&c->wimg_snap, img_bytes);
     if (e != cudaSuccess) return cuda_status(e, "nrc_frame_host pipeline set-up");
   }
   cudaEvent_t ev_start = c->ev_pipe[0], ev_snap = c->ev_pipe[1], ev_pool = c->ev_pipe[2], ev_train = c->ev_pipe[3];
@@ -526,7 +546,7 @@ nrc_status nrc_frame_host(nrc_cache* c, const float* queries, int64_t n_q, float
     cudaFree(c->stage);
     c->stage = nullptr;
     c->stage_bytes = 0;
-    cudaError_t e = cudaMalloc(&c->stage, need);
+    cudaError_t e = dev_alloc(&c->stage, need);
     if (e != cudaSuccess) return cuda_status(e, "nrc_frame_host staging");
     c->stage_bytes = need;
   }
@@ -607,6 +627,19 @@ nrc_status nrc_set_ema(nrc_cache* c, const float* ema, nrc_stream stream) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   c->wimg8_dirty = true;
   return cuda_status(e, "nrc_set_ema");
+}
+
+void nrc_debug_fail_device_allocs(int32_t after, int32_t count) {
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  g_alloc_skip = after > 0 ? after : 0;
+  g_alloc_fail = count > 0 ? count : 0;
+}
+
+nrc_status nrc_debug_wait_timeout(nrc_cache* c, int32_t limit_us, nrc_stream stream) {
+  if (!c) return set_error("cache is NULL"), NRC_ERR_INVALID_ARG;
+  if (limit_us < 1 || limit_us > 2000000) return set_error("limit_us must be in [1, 2000000]"), NRC_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  return cuda_status(launch_wait_probe(c->err, 1000ull * (unsigned long long)limit_us, st), "nrc_debug_wait_timeout");
 }
 
 nrc_status nrc_check_error(nrc_cache* c, nrc_stream stream) {

@@ -76,12 +76,12 @@ nrc_status batch_init(Batch* b, const nrc_cache* proto, int max_caches) {
   b->max_units = 1 << 16;
   b->stride = partial_stride(proto->net.n_params);
   b->slot_bytes = slot_size(b);
-  cudaError_t e = cudaMalloc(&b->d_caches, sizeof(BatchCache) * max_caches);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_units, sizeof(BatchUnit) * b->max_units);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(unsigned));
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_jobs, sizeof(TrainJob) * b->max_jobs);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_adam, sizeof(AdamJob) * max_caches);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_partials, size_t(b->max_jobs) * b->stride * 4);
+  cudaError_t e = dev_alloc(&b->d_caches, sizeof(BatchCache) * max_caches);
+  if (e == cudaSuccess) e = dev_alloc(&b->d_units, sizeof(BatchUnit) * b->max_units);
+  if (e == cudaSuccess) e = dev_alloc(&b->d_counter, sizeof(unsigned));
+  if (e == cudaSuccess) e = dev_alloc(&b->d_jobs, sizeof(TrainJob) * b->max_jobs);
+  if (e == cudaSuccess) e = dev_alloc(&b->d_adam, sizeof(AdamJob) * max_caches);
+  if (e == cudaSuccess) e = dev_alloc(&b->d_partials, size_t(b->max_jobs) * b->stride * 4);
   if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&b->pinned), b->slot_bytes * kRing, cudaHostAllocDefault);
   for (int i = 0; i < kRing && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&b->ev[i], cudaEventDisableTiming);
   if (e != cudaSuccess) {
@@ -107,8 +107,8 @@ static nrc_status reserve_jobs(Batch* b, int n_jobs, cudaStream_t st) {
   b->pinned = nullptr;
   b->max_jobs = n_jobs;
   b->slot_bytes = slot_size(b);
-  e = cudaMalloc(&b->d_jobs, sizeof(TrainJob) * b->max_jobs);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_partials, size_t(b->max_jobs) * b->stride * 4);
+  e = dev_alloc(&b->d_jobs, sizeof(TrainJob) * b->max_jobs);
+  if (e == cudaSuccess) e = dev_alloc(&b->d_partials, size_t(b->max_jobs) * b->stride * 4);
   if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&b->pinned), b->slot_bytes * kRing, cudaHostAllocDefault);
   if (e != cudaSuccess) {
     b->max_jobs = 0;

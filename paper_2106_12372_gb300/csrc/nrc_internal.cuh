@@ -23,6 +23,17 @@ constexpr int kErrTimeout = 1;
 // Bounded device waits give up after this many nanoseconds.
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;
 
+// Fault injection for tests (nrc_debug_fail_device_allocs): after
+// g_alloc_skip more device allocations, the next g_alloc_fail ones fail as if
+// the device were out of memory.
+extern int g_alloc_skip, g_alloc_fail;
+cudaError_t dev_alloc_bytes(void** p, size_t bytes);
+// Every device allocation of the library goes through here.
+template <class T>
+inline cudaError_t dev_alloc(T** p, size_t bytes) {
+  return dev_alloc_bytes(reinterpret_cast<void**>(p), bytes);
+}
+
 struct NetShape {
   int n_mats;              // hidden_layers + 1
   int dims[kMaxMats + 1];  // d_0 = 64, d_1..d_H = width, d_L = 3
@@ -164,6 +175,9 @@ cudaError_t launch_build_image_of(const Cache* c, const float* w, uint8_t* img, 
 inline const float* query_weights(const Cache* c) { return c->cfg.ema ? c->ema : c->w; }
 inline const uint8_t* query_image(const Cache* c) { return c->cfg.ema ? c->wimg_ema : c->wimg; }
 cudaError_t launch_step_increment(Cache* c, cudaStream_t st);
+// Waits, through the kernels' bounded mbarrier wait, on an mbarrier that
+// nothing arrives at; gives up after limit_ns and sets kErrTimeout in *err.
+cudaError_t launch_wait_probe(int* err, unsigned long long limit_ns, cudaStream_t st);
 // image: the weight image to read (nullptr: the cache's queried image)
 cudaError_t launch_infer_tc(Cache* c, const float* rec, int64_t n, float* rgb, cudaStream_t st,
                             const uint8_t* image = nullptr);

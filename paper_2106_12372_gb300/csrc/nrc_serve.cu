@@ -369,7 +369,7 @@ nrc_status nrc_server_open_viewport(nrc_server* s, const nrc_config* cache_cfg, 
     s->used += need;
   }
   void* blk = nullptr;
-  cudaError_t e = cudaMalloc(&blk, block_b);
+  cudaError_t e = dev_alloc(&blk, block_b);
   if (e != cudaSuccess) {
     cudaGetLastError();
     release(c, nullptr, need);

@@ -36,17 +36,18 @@ __device__ __forceinline__ uint32_t mbar_try_wait(uint32_t bar, uint32_t parity)
   return ok;
 }
 
-// Waits for phase `parity` of `bar` to complete.  Gives up after
-// kWaitLimitNs (or at once when the error word is already set), setting
-// kErrTimeout in *err; returns false then.  Never spins without a bound.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+// Waits for phase `parity` of `bar` to complete.  Gives up after limit_ns
+// (or at once when the error word is already set), setting kErrTimeout in
+// *err; returns false then.  Never spins without a bound.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err,
+                                          unsigned long long limit_ns = kWaitLimitNs) {
   const uint32_t a = smem_u32(bar);
   if (mbar_try_wait(a, parity)) return true;
   const unsigned long long t0 = globaltimer_ns();
   while (true) {
     if (mbar_try_wait(a, parity)) return true;
     if (*reinterpret_cast<volatile int*>(err) != 0) return false;
-    if (globaltimer_ns() - t0 > kWaitLimitNs) {
+    if (globaltimer_ns() - t0 > limit_ns) {
       atomicOr(err, kErrTimeout);
       return false;
     }

@@ -131,6 +131,8 @@ def lib() -> ctypes.CDLL:
             "nrc_set_state": (i32, [P, P, P, P, i64, P]),
             "nrc_set_path": (i32, [P, i32]),
             "nrc_check_error": (i32, [P, P]),
+            "nrc_debug_fail_device_allocs": (None, [i32, i32]),
+            "nrc_debug_wait_timeout": (i32, [P, i32, P]),
             "nrc_launch_count": (i64, [P]),
             "nrc_last_error_string": (ctypes.c_char_p, []),
             "nrc_train_step_noalloc": (i32, [P, P, P, P, P, P, P, i64, i64, u64, i32, P, P, P]),
@@ -317,6 +319,11 @@ class Cache:
         a = np.ascontiguousarray(ema, dtype=np.float32)
         _check(lib().nrc_set_ema(self._h, a.ctypes.data, _stream(stream)))
 
+    def debug_wait_timeout(self, limit_us: int, stream=None) -> None:
+        """Fault injection: a bounded device wait that runs out after limit_us
+        (the next check_error raises NRC_ERR_TIMEOUT)."""
+        _check(lib().nrc_debug_wait_timeout(self._h, int(limit_us), _stream(stream)))
+
     def check_error(self, stream=None) -> None:
         _check(lib().nrc_check_error(self._h, _stream(stream)))
 
@@ -497,6 +504,12 @@ class _Paths(ctypes.Structure):
 class PathParams(ctypes.Structure):
     _fields_ = [("c", ctypes.c_float), ("tile", ctypes.c_int32), ("tile_ox", ctypes.c_int32),
                 ("tile_oy", ctypes.c_int32), ("unbiased_phase", ctypes.c_int32), ("rr_survive", ctypes.c_float)]
+
+
+def debug_fail_device_allocs(after: int, count: int) -> None:
+    """Fault injection: after `after` more device allocations by the library,
+    the next `count` fail as if out of memory; (0, 0) switches it off."""
+    lib().nrc_debug_fail_device_allocs(int(after), int(count))
 
 
 def paths_tile_count(width: int, height: int, tile: int) -> int:
