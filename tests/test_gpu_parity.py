@@ -160,6 +160,33 @@ def _one_step(dtype, n_pool, batch, step, seed, loss_mode=0, mode=0):
     return ref_loss, ref_g, st, loss.item(), w, m, v, t
 
 
+# The small configuration as one workload: 65,536 queries and one training step
+# of 16,384 records from a 16,384-record pool, FP32 against the FP64 oracle, pad
+# value 1 (Sec. 3.6) and 0, seeds 2107.
+@pytest.mark.parametrize("pad", [1.0, 0.0])
+def test_small_config_frame_fp32(pad):
+    seed = 2107
+    w0 = synth.xavier_weights(DIMS, seed=seed)
+    q = synth.make_records(65536, seed=seed)
+    pool, tgt = synth.make_training_pool(16384, seed=seed + 1)
+    fs = synth.frame_seed(seed, 0)
+    cache = nrc.Cache(dtype="fp32", pad_value=pad)
+    cache.set_state(w0)
+    rgb = torch.empty((65536, 3), device=DEV)
+    loss = torch.zeros(1, device=DEV)
+    cache.frame(dev(q), rgb, dev(pool), dev(tgt), 16384, 1, fs, loss_out=loss)
+    cache.check_error()
+    ref_rgb = O.infer(w0, DIMS, q, pad_value=pad)
+    assert rel_err(rgb.cpu().numpy(), ref_rgb).max() <= 1e-5, stats(rgb.cpu().numpy(), ref_rgb)
+    st = O.TrainState(w0, DIMS)
+    ref_loss, ref_g = st.step(pool, tgt, 16384, fs, 0, pad_value=pad, want_grad=True)
+    assert abs(loss.item() - ref_loss) <= 1e-5 * abs(ref_loss)
+    _, m, _, t = cache.get_state()
+    assert t == 1
+    g = m.astype(np.float64) / (1.0 - 0.9)  # after step 1, m = (1 - beta1) g
+    assert rel_err(g, ref_g).max() <= 1e-5, stats(g, ref_g)
+
+
 @pytest.mark.parametrize("n_pool,batch,step", [(4096, 1024, 2), (1000, 333, 2), (16384, 16384, 0)])
 @pytest.mark.parametrize("loss_mode", [0, 1])
 def test_train_step_fp32(n_pool, batch, step, loss_mode):
