@@ -382,6 +382,14 @@ NRC_API nrc_status nrc_server_submit(nrc_server* server, int32_t id, int32_t slo
 NRC_API nrc_status nrc_server_poll(nrc_server* server, nrc_frame_done* out, int32_t max_out, int32_t timeout_ms,
                                    int32_t* n_out);
 
+/* Holds (paused != 0) or releases (0) the scheduler: while held, submitted
+ * frames wait and no batch is issued; on release the pending frames are
+ * batched as usual (in arrival order, at most one per viewport per batch).
+ * A renderer can hold, submit every viewport's frame of a display interval
+ * and release them into one batch.  nrc_server_drain,
+ * nrc_server_close_viewport and nrc_server_destroy release a held server. */
+NRC_API nrc_status nrc_server_pause(nrc_server* server, int32_t paused);
+
 /* Blocks until every submitted frame is done and the stream is idle. */
 NRC_API nrc_status nrc_server_drain(nrc_server* server);
 

@@ -90,6 +90,7 @@ struct Server {
   std::deque<nrc_frame_done> done;
   int inflight = 0;
   bool stop = false;
+  bool paused = false;  // nrc_server_pause: submitted frames wait, no batch is issued
   std::mutex mu;
   std::condition_variable cv;
   std::thread thr;
@@ -172,7 +173,9 @@ static void scheduler(Server* s) {
     std::vector<Frame> fr;
     {
       std::unique_lock<std::mutex> lk(s->mu);
-      s->cv.wait(lk, [s] { return s->stop || (!s->pending.empty() && s->inflight < s->cfg.max_inflight); });
+      s->cv.wait(lk, [s] {
+        return s->stop || (!s->paused && !s->pending.empty() && s->inflight < s->cfg.max_inflight);
+      });
       if (s->stop) return;
       std::vector<char> taken(s->vps.size(), 0);
       for (auto it = s->pending.begin(); it != s->pending.end();) {
@@ -282,10 +285,22 @@ nrc_status nrc_server_create(const nrc_server_config* cfg, const nrc_config* cac
   return NRC_OK;
 }
 
+nrc_status nrc_server_pause(nrc_server* s, int32_t paused) {
+  if (!s) return set_error("server is NULL"), NRC_ERR_INVALID_ARG;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->paused = paused != 0;
+  }
+  s->cv.notify_all();
+  return NRC_OK;
+}
+
 nrc_status nrc_server_drain(nrc_server* s) {
   if (!s) return set_error("server is NULL"), NRC_ERR_INVALID_ARG;
   {
     std::unique_lock<std::mutex> lk(s->mu);
+    s->paused = false;  // held frames are released
+    s->cv.notify_all();
     s->cv.wait(lk, [s] { return s->pending.empty() && s->inflight == 0; });
   }
   cudaError_t e = cudaStreamSynchronize(s->st);
@@ -415,6 +430,8 @@ nrc_status nrc_server_close_viewport(nrc_server* s, int32_t id) {
   {
     std::unique_lock<std::mutex> lk(s->mu);
     if (!s->vps[size_t(id)].open) return set_error("nrc_server_close_viewport: viewport %d is not open", id), NRC_ERR_INVALID_ARG;
+    s->paused = false;  // its held frames are released
+    s->cv.notify_all();
     s->cv.wait(lk, [s, id] { return s->vps[size_t(id)].queued == 0; });
     v = s->vps[size_t(id)];
     s->vps[size_t(id)].open = false;

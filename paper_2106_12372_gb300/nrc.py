@@ -161,6 +161,7 @@ def lib() -> ctypes.CDLL:
             "nrc_server_viewport_pool": (i32, [P, i32, P, P, P]),
             "nrc_server_submit": (i32, [P, i32, i32, i64, u64, i64, i64]),
             "nrc_server_poll": (i32, [P, P, i32, i32, P]),
+            "nrc_server_pause": (i32, [P, i32]),
             "nrc_server_drain": (i32, [P]),
             "nrc_server_query": (i32, [P, P]),
         }
@@ -486,6 +487,10 @@ class Server:
         n = ctypes.c_int32()
         _check(lib().nrc_server_poll(self._h, buf, max_out, timeout_ms, ctypes.byref(n)))
         return [buf[i] for i in range(n.value)]
+
+    def pause(self, paused: bool = True) -> None:
+        """Holds (or releases) the scheduler: held frames are batched together on release."""
+        _check(lib().nrc_server_pause(self._h, int(bool(paused))))
 
     def drain(self) -> None:
         _check(lib().nrc_server_drain(self._h))

@@ -10,6 +10,8 @@
   once another closes; a slot still in flight refuses a new frame;
 * a short Poisson-arrival run completes every frame with sane timings.
 """
+import time
+
 import numpy as np
 import pytest
 
@@ -88,6 +90,8 @@ def _run_x(srv, x, others):
     for f in range(FRAMES):
         slot = f % 2
         order = [vid for vid, _ in others] + [x]  # X last: it joins frames already pending
+        if others:
+            srv.pause(True)  # the round's frames are released together: X shares their batch
         for vid in order:
             while (vid, slot) in pending:
                 collect(True)
@@ -98,6 +102,7 @@ def _run_x(srv, x, others):
                 ok = srv.submit(vid, slot, other_recs[vid][1], synth.frame_seed(vid, f), tag=f)
             assert ok
             pending[(vid, slot)] = True
+        srv.pause(False)
     srv.drain()
     while len(outs) < FRAMES or pending:
         collect(True)
@@ -211,3 +216,33 @@ def test_poisson_run_completes():
     assert np.all(lat > 0) and np.all(lat < 1000)
     assert all(d.launch_ns >= d.submit_ns and d.done_ns >= d.launch_ns for d in done)
     print("poisson frames", len(done), "p50 ms", np.percentile(lat, 50), "p99 ms", np.percentile(lat, 99))
+
+
+def test_pause_holds_frames_until_released():
+    srv = _server()
+    vids = [srv.open_viewport(5000, STEPS * TBATCH, seed=s) for s in (31, 32, 33)]
+    for k, v in enumerate(vids):
+        _fill_pool(srv, v, seed=31 + k)
+        _write(srv, v, 0, synth.make_records(5000, seed=40 + k))
+    srv.pause(True)
+    for v in vids:
+        assert srv.submit(v, 0, 5000, synth.frame_seed(v, 0), tag=v)
+    time.sleep(0.05)
+    assert srv.poll(timeout_ms=20) == []  # held
+    srv.pause(False)
+    done = []
+    while len(done) < 3:
+        got = srv.poll(timeout_ms=2000)
+        assert got, "released frames did not complete"
+        done += got
+    assert all(d.batch_frames == 3 for d in done)  # one batch
+    # drain releases a held server
+    for v in vids:
+        _write(srv, v, 1, synth.make_records(5000, seed=50))
+    srv.pause(True)
+    for v in vids:
+        assert srv.submit(v, 1, 5000, synth.frame_seed(v, 1), tag=10 + v)
+    srv.drain()
+    assert len(srv.poll(timeout_ms=0)) == 3
+    srv.close()
+
