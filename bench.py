@@ -507,9 +507,15 @@ def run_serving(queries, dtype: str, seconds: float):
     torch.cuda.synchronize()
     info0 = srv.info()
     # warm-up: two frames per viewport
+    def wait_slot(t_end):
+        if time.monotonic() > t_end:
+            raise RuntimeError("serving: a frame slot stayed busy for 30 s")
+
     for f in range(2):
         for vid, n, _ in vps:
+            t_end = time.monotonic() + 30.0
             while not srv.submit(vid, f % 2, n, synth.frame_seed(vid, f)):
+                wait_slot(t_end)
                 srv.poll(timeout_ms=5)
     srv.drain()
     srv.poll(max_out=4096)
@@ -530,7 +536,9 @@ def run_serving(queries, dtype: str, seconds: float):
             if due - nrc.now_ns() > 300_000:
                 time.sleep(0.0001)
         f = nxt[vid]
+        t_end = time.monotonic() + 30.0
         while not srv.submit(vid, f % 2, n, synth.frame_seed(vid, f), arrival_ns=due, tag=f):
+            wait_slot(t_end)
             done += srv.poll(timeout_ms=1)
         nxt[vid] += 1
     srv.drain()

@@ -77,7 +77,10 @@ def _run_x(srv, x, others):
     pending = {}
 
     def collect(block):
-        for d in srv.poll(timeout_ms=2000 if block else 0):
+        got = srv.poll(timeout_ms=2000 if block else 0)
+        if block and not got:
+            raise AssertionError("no frame completed within 2 s")
+        for d in got:
             assert not d.failed
             if d.viewport == x:
                 _, rgb, ls = srv.buffers(x, d.slot)
@@ -90,11 +93,12 @@ def _run_x(srv, x, others):
     for f in range(FRAMES):
         slot = f % 2
         order = [vid for vid, _ in others] + [x]  # X last: it joins frames already pending
+        for vid in order:  # the slot's previous frames finish first (the server is not held)
+            while (vid, slot) in pending:
+                collect(True)
         if others:
             srv.pause(True)  # the round's frames are released together: X shares their batch
         for vid in order:
-            while (vid, slot) in pending:
-                collect(True)
             if vid == x:
                 _write(srv, x, slot, X_RECS[f])
                 ok = srv.submit(x, slot, X_N, synth.frame_seed(X_SEED, f), tag=f)
@@ -193,8 +197,6 @@ def test_poisson_run_completes():
             arrivals.append((t, vid, n))
             t += rng.exponential(1 / rate)
     arrivals.sort()
-    import time
-
     t0 = nrc.now_ns()
     nxt = {vid: 0 for vid, _, _ in vps}
     busy = {}
@@ -204,7 +206,9 @@ def test_poisson_run_completes():
             done += srv.poll(timeout_ms=0)
             time.sleep(0.0002)
         slot = nxt[vid] % 2
+        deadline = time.monotonic() + 10.0
         while not srv.submit(vid, slot, n, synth.frame_seed(vid, nxt[vid]), arrival_ns=t0 + int(t * 1e9)):
+            assert time.monotonic() < deadline, "slot never freed"
             done += srv.poll(timeout_ms=5)
         nxt[vid] += 1
         busy[vid] = True
