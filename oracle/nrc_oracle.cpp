@@ -3,11 +3,11 @@
 // Path Tracing", ACM TOG 40(4), 2021).
 //
 // TEST INFRASTRUCTURE.  Only the tests, the package's smoke check and the
-// benchmark's CPU-baseline leg may load or call this library.  The product
-// path (the CUDA library) never links, imports or calls it, and the two share
-// no code: every step below is written out from the paper's definitions, in
-// plain loops, in double precision.  Inputs arrive as FP32 (records, targets,
-// weights) and are promoted to FP64.
+// benchmark's CPU-baseline and reference legs may load or call this library.
+// The product path (the CUDA library) never links, imports or calls it, and
+// the two share no code: every step below is written out from the paper's
+// definitions, in plain loops, in double precision.  Inputs arrive as FP32
+// (records, targets, weights) and are promoted to FP64.
 //
 // Steps and the passages they follow:
 //   * training-record shuffle by a linear congruential map  - Sec. 3.5

@@ -1,8 +1,9 @@
 """Python access to the FP64 CPU oracle (``nrc_oracle.cpp``).
 
 TEST INFRASTRUCTURE.  Only the tests, the package's smoke check and the
-benchmark's CPU-baseline leg may import this module.  The CUDA library and its
-binding never import it; the two implementations share no code.
+benchmark's CPU-baseline and reference legs may import this module.  The CUDA
+library and its binding never import it; the two implementations share no
+code.
 
 Every function takes numpy arrays, promotes FP32 inputs to FP64 exactly as the
 C code does, and returns FP64 results.  See the C source for the passage of
