@@ -401,9 +401,10 @@ def run_paths(dtype: str, flush, frames: int = 20):
     termination heuristic of Eqs. 3-4): terminate every pixel's path and pick
     the training paths, query the cache at the terminal vertices and at the
     training paths' tails, build the self-training records, train 4 steps of
-    16,384 records on them and composite the pixels.  The tile side is adapted
-    during the warm-up frames toward 65,536 training records and then held;
-    each stage is timed with CUDA events."""
+    16,384 records on them and composite the pixels.  The tail queries sit
+    after the render queries in one buffer, so one query launch answers both.
+    The tile side is adapted during the warm-up frames toward 65,536 training
+    records and then held; each stage is timed with CUDA events."""
     import numpy as np
     import torch
 
@@ -419,10 +420,8 @@ def run_paths(dtype: str, flush, frames: int = 20):
     cache = nrc.Cache(dtype=dtype, seed=2106)
     cam = synth.PATH_CAMERA
     P = W * H
-    rq = torch.empty((P, 16), device=dev)
     em = torch.empty((P, 3), device=dev)
     tp = torch.empty((P, 3), device=dev)
-    rgb = torch.empty((P, 3), device=dev)
     img = torch.empty((P, 3), device=dev)
     pool = torch.zeros((N_POOL, 16), device=dev)
     tg = torch.zeros((N_POOL, 3), device=dev)
@@ -438,11 +437,14 @@ def run_paths(dtype: str, flush, frames: int = 20):
         tile = nrc.paths_adapt_tile(tile, n, N_POOL)
     nt = nrc.paths_tile_count(W, H, tile)
     tiles = torch.empty((nt, 4), dtype=torch.int32, device=dev)
-    tq = torch.zeros((nt, 16), device=dev)
-    tail = torch.empty((nt, 3), device=dev)
+    # the tail queries follow the render queries in one buffer: one query launch answers both
+    q_all = torch.zeros((P + nt, 16), device=dev)
+    rgb_all = torch.empty((P + nt, 3), device=dev)
+    rq, tq = q_all[:P], q_all[P:]
+    rgb, tail = rgb_all[:P], rgb_all[P:]
     offsets = torch.empty(nrc.paths_offsets_count(nt), dtype=torch.int64, device=dev)
     st = torch.cuda.current_stream()
-    names = ("terminate", "render_queries", "tail_queries", "records", "train", "composite")
+    names = ("terminate", "queries", "records", "train", "composite")
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)] for _ in range(frames + 3)]
     counts = torch.zeros(frames + 3, dtype=torch.int64, device=dev)
     for f, e in enumerate(ev):
@@ -451,16 +453,14 @@ def run_paths(dtype: str, flush, frames: int = 20):
         e[0].record(st)
         nrc.paths_terminate(v, W, H, cam, prm, out=(rq, em, tp, tiles, tq))
         e[1].record(st)
-        cache.infer(rq, rgb)
+        cache.infer(q_all, rgb_all)
         e[2].record(st)
-        cache.infer(tq, tail)
-        e[3].record(st)
         nrc.paths_records(v, W, H, cam, prm, tiles, tail, N_POOL, out=(pool, tg, offsets, count))
-        e[4].record(st)
+        e[3].record(st)
         cache.frame(rq[:0], rgb[:0], pool, tg, BATCH, N_STEPS, synth.frame_seed(2106 + 3, f))
-        e[5].record(st)
+        e[4].record(st)
         nrc.paths_composite(em, tp, rgb, out=img)
-        e[6].record(st)
+        e[5].record(st)
         counts[f] = count[0]
     torch.cuda.synchronize()
     cache.check_error()

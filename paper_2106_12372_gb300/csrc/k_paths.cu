@@ -27,12 +27,6 @@ __device__ __forceinline__ float d2_rn(const float* a, const float* b) {
   return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
 }
 
-// A path's vertex j, from global memory.
-struct GlobalPath {
-  const float* g;
-  __device__ __forceinline__ const float* operator()(int j) const { return g + j * kVtx; }
-};
-
 // A path whose vertices 0 and 1 are staged in shared memory (the rest stays in
 // global memory).
 struct StagedPath {
@@ -85,6 +79,24 @@ struct PathsArgs {
   int tiles_x, n_tiles;
 };
 
+// End of a training path's suffix from x_n (Sec. 3.4/3.5): the first x_m
+// past the spread threshold (the sum restarted at x_n), or -- for a
+// roulette-only suffix -- where the roulette stops it.
+template <class V>
+__device__ __forceinline__ int suffix_end(const V& v, int K, float thr, int n, bool unb, float q) {
+  if (unb) {
+    for (int j = n; j < K; ++j)
+      if (j == K - 1 || !(v(j)[22] < q)) return j;
+    return K - 1;
+  }
+  float acc = 0.0f;
+  for (int j = n + 1; j < K; ++j) {
+    acc = __fadd_rn(acc, spread_term(v, j));
+    if (__fmul_rn(acc, acc) > thr) return j;
+  }
+  return K - 1;
+}
+
 // One warp per 32 consecutive pixels.  Vertices 0 and 1 of its pixels (the
 // first 192 bytes of each path; the rendering path ends at vertex 1 for most
 // pixels) are staged in shared memory with coalesced 16-byte loads, and the
@@ -96,7 +108,7 @@ constexpr int kOutStride = kRecFloats + 1;
 
 __global__ void __launch_bounds__(kRenderWarps * 32)
     k_paths_render(const __grid_constant__ PathsArgs a, float* __restrict__ rq, float* __restrict__ emitted,
-                   float* __restrict__ throughput) {
+                   float* __restrict__ throughput, int* __restrict__ tiles, float* __restrict__ tq) {
   __shared__ float stage[kRenderWarps][32 * kStageStride];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t P = int64_t(a.width) * a.height;
@@ -104,6 +116,14 @@ __global__ void __launch_bounds__(kRenderWarps * 32)
   if (p0 >= P) return;  // the whole warp
   const int valid = P - p0 < 32 ? int(P - p0) : 32;
   const int64_t path_floats = int64_t(a.K) * kVtx;
+  {  // a tile whose training pixel lies outside the image has no training path
+    const int64_t g = p0 + lane;
+    if (g < a.n_tiles) {
+      const int ty = int(g / a.tiles_x), tx = int(g - int64_t(ty) * a.tiles_x);
+      if (tx * a.tile + a.ox >= a.width || ty * a.tile + a.oy >= a.height)
+        reinterpret_cast<int4*>(tiles)[g] = make_int4(-1, 0, 0, 0);
+    }
+  }
   float* sm = stage[warp];
   {  // 12 float4 per pixel = vertices 0 and 1; all of a lane's loads in flight at once
     float4 x[12];
@@ -128,7 +148,18 @@ __global__ void __launch_bounds__(kRenderWarps * 32)
   float rec[14], E[3] = {0.0f, 0.0f, 0.0f}, T[3] = {1.0f, 1.0f, 1.0f};
   if (lane < valid) {
     const StagedPath v{sm + lane * kStageStride, a.vtx + (p0 + lane) * path_floats};
-    const int n = render_end(v, a.K, spread_threshold(v, a.cam, a.c));
+    const float thr = spread_threshold(v, a.cam, a.c);
+    const int n = render_end(v, a.K, thr);
+    // the training pixel of its tile: the tile's entry and the tail's query record
+    const int64_t p = p0 + lane;
+    const int py = int(p / a.width), px = int(p - int64_t(py) * a.width);
+    if (px >= a.ox && py >= a.oy && (px - a.ox) % a.tile == 0 && (py - a.oy) % a.tile == 0) {
+      const int t = ((py - a.oy) / a.tile) * a.tiles_x + (px - a.ox) / a.tile;
+      const bool unb = a.phase >= 0 && t % 16 == a.phase;
+      const int m = suffix_end(v, a.K, thr, n, unb, a.q);
+      reinterpret_cast<int4*>(tiles)[t] = make_int4(int(p), n, m, unb ? 1 : 0);
+      write_record(tq + int64_t(t) * kRecFloats, v(m));
+    }
     for (int j = 0; j <= n; ++j) {
       const float* vj = v(j);
 #pragma unroll
@@ -166,43 +197,6 @@ __global__ void __launch_bounds__(kRenderWarps * 32)
     emitted[p0 * 3 + i] = so[i];
     throughput[p0 * 3 + i] = so[96 + i];
   }
-}
-
-// tiles[t] = {pixel (-1: none), n, m, unbiased}; the tail query of a training path
-__global__ void k_paths_tiles(const __grid_constant__ PathsArgs a, int* __restrict__ tiles, float* __restrict__ tq) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= a.n_tiles) return;
-  const int ty = t / a.tiles_x, tx = t % a.tiles_x;
-  const int px = tx * a.tile + a.ox, py = ty * a.tile + a.oy;
-  int4 info = make_int4(-1, 0, 0, 0);
-  if (px < a.width && py < a.height) {
-    const int64_t p = int64_t(py) * a.width + px;
-    const float* v = a.vtx + p * a.K * kVtx;
-    const GlobalPath gp{v};
-    const float thr = spread_threshold(gp, a.cam, a.c);
-    const int n = render_end(gp, a.K, thr);
-    const bool unb = a.phase >= 0 && t % 16 == a.phase;
-    int m = a.K - 1;
-    if (unb) {
-      for (int j = n; j < a.K; ++j)
-        if (j == a.K - 1 || !(v[j * kVtx + 22] < a.q)) {
-          m = j;
-          break;
-        }
-    } else {
-      float acc = 0.0f;
-      for (int j = n + 1; j < a.K; ++j) {
-        acc = __fadd_rn(acc, spread_term(gp, j));
-        if (__fmul_rn(acc, acc) > thr) {
-          m = j;
-          break;
-        }
-      }
-    }
-    info = make_int4(int(p), n, m, unb ? 1 : 0);
-    write_record(tq + int64_t(t) * kRecFloats, v + m * kVtx);
-  }
-  reinterpret_cast<int4*>(tiles)[t] = info;
 }
 
 // Exclusive scan of the records per training path (m of them) in tile order,
@@ -410,8 +404,7 @@ nrc_status nrc_paths_terminate(const nrc_paths* paths, const nrc_path_params* pa
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int64_t P = int64_t(a.width) * a.height;
   k_paths_render<<<unsigned((P + kRenderWarps * 32 - 1) / (kRenderWarps * 32)), kRenderWarps * 32, 0, st>>>(
-      a, render_queries, render_emitted, render_throughput);
-  k_paths_tiles<<<unsigned((a.n_tiles + 255) / 256), 256, 0, st>>>(a, tiles, tail_queries);
+      a, render_queries, render_emitted, render_throughput, tiles, tail_queries);
   return cuda_status(cudaGetLastError(), "nrc_paths_terminate");
 }
 

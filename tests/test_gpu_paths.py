@@ -138,3 +138,23 @@ def test_preallocated_outputs_match(scene):
                        nrc.paths_composite(ref[1], ref[2], tail[:1].expand(W * H, 3).contiguous()))
     with pytest.raises(ValueError):
         nrc.paths_terminate(V, W, H, synth.PATH_CAMERA, prm, out=(out[0][:10],) + out[1:])
+
+
+def test_tail_queries_in_the_render_buffer():
+    # the tail queries written after the render queries in one buffer, answered
+    # by one query launch, equal the separate buffers and launches
+    v = synth.make_paths(W, H, K, seed=21)
+    V = torch.from_numpy(v).to(DEV)
+    prm = _params(tile=5, ox=1, oy=4, phase=2)
+    rq, em, tp, tiles, tq = nrc.paths_terminate(V, W, H, synth.PATH_CAMERA, prm)
+    nt = nrc.paths_tile_count(W, H, 5)
+    P = W * H
+    q_all = torch.zeros((P + nt, 16), device=DEV)
+    t2 = torch.empty((nt, 4), dtype=torch.int32, device=DEV)
+    nrc.paths_terminate(V, W, H, synth.PATH_CAMERA, prm,
+                        out=(q_all[:P], torch.empty_like(em), torch.empty_like(tp), t2, q_all[P:]))
+    assert torch.equal(q_all[:P], rq) and torch.equal(q_all[P:], tq) and torch.equal(t2, tiles)
+    c = nrc.Cache(dtype="fp16", seed=27)
+    both = c.infer(q_all)
+    assert torch.equal(both[:P], c.infer(rq)) and torch.equal(both[P:], c.infer(tq))
+    c.check_error()
