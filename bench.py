@@ -477,6 +477,58 @@ def run_paths(dtype: str, flush, frames: int = 20):
     return out
 
 
+SMALL_Q, SMALL_B = 65536, 16384
+
+
+def run_small(flush, frames: int = 20):
+    """The small configuration: 65,536 queries and one training step of
+    16,384 records from a 16,384-record pool, in FP32, on the fused (SIMT)
+    path and on the plain per-layer path; ms per frame (median)."""
+    import numpy as np
+    import torch
+
+    from paper_2106_12372_gb300 import nrc, synth
+
+    dev = torch.device("cuda:0")
+    q = torch.from_numpy(synth.make_records(SMALL_Q, seed=2107)).to(dev)
+    pool, tgt = (torch.from_numpy(x).to(dev) for x in synth.make_training_pool(SMALL_B, seed=2108))
+    rgb = torch.empty((SMALL_Q, 3), device=dev)
+    st = torch.cuda.current_stream()
+    out = {}
+    for name, path in (("fused_fp32", nrc.PATH_FUSED), ("plain_fp32", nrc.PATH_PLAIN)):
+        c = nrc.Cache(dtype="fp32", path=path, seed=2107)
+        for k in range(3):
+            c.frame(q, rgb, pool, tgt, SMALL_B, 1, synth.frame_seed(2107, k))
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(frames)]
+        for k, e in enumerate(ev):
+            flush.zero_()
+            e[0].record(st)
+            c.frame(q, rgb, pool, tgt, SMALL_B, 1, synth.frame_seed(2107, 3 + k))
+            e[1].record(st)
+        torch.cuda.synchronize()
+        c.check_error()
+        out[name + "_ms"] = float(np.median([e[0].elapsed_time(e[1]) for e in ev]))
+        c.close()
+    out["workload"] = "65,536 queries + 1 step of 16,384 records from a 16,384-record pool, FP32"
+    return out
+
+
+def cpu_oracle_small(seed: int = 2107):
+    """The FP64 oracle on one whole small-configuration frame (ms, cores)."""
+    from oracle import oracle as O
+    from paper_2106_12372_gb300 import synth
+
+    dims = synth.layer_dims()
+    q = synth.make_records(SMALL_Q, seed=seed)
+    pool, tgt = synth.make_training_pool(SMALL_B, seed=seed + 1)
+    st = O.TrainState(synth.xavier_weights(dims, seed=seed), dims)
+    O.infer(st.W, dims, q[:1024])  # load the library and its threads
+    t0 = time.perf_counter()
+    O.infer(st.W, dims, q)
+    st.step(pool, tgt, SMALL_B, synth.frame_seed(seed, 0), 0)
+    return (time.perf_counter() - t0) * 1e3, int(os.environ.get("ORACLE_THREADS", os.cpu_count() or 1))
+
+
 def run_serving(queries, dtype: str, seconds: float):
     """Eight viewports (4 x 1920x1080, 4 x 3840x2160) with Poisson frame
     arrivals at 30-120 Hz each (rates seeded), served by the continuous-
@@ -641,13 +693,14 @@ def run_gpu(args):
             plain_ms.append(pev[0].elapsed_time(pev[1]))
     plain.close()
 
-    batched = serving = shampoo = precision = paths = None
+    batched = serving = shampoo = precision = paths = small = None
     if not args.no_extras and ws == 1 and args.dtype != "fp32":
         batched = run_batched(queries, args.dtype, 30, flush)
         serving = run_serving(queries, args.dtype, args.serve_seconds)
         shampoo = run_shampoo(pool, tgt, args.dtype, 30, flush)
         precision = run_precision(queries, flush)
         paths = run_paths(args.dtype, flush)
+        small = run_small(flush)
 
     # end to end: host (pinned) buffers through nrc_frame_host, copies inside the timed region
     qh = torch.from_numpy(synth.make_records(N_QUERIES, seed=seed + 7)).pin_memory()
@@ -677,6 +730,8 @@ def run_gpu(args):
     if not args.no_cpu_baseline and ws == 1:
         v, d, cores, _ = cpu_oracle_frame(args.cpu_budget)
         cpu = {"value": v, "unit": "Mqueries/s", "cores": cores, "kind": "oracle", "sample": d}
+        if small is not None:
+            small["oracle_fp64_ms"], small["oracle_cores"] = cpu_oracle_small()
     line = {
         "metric": METRIC, "value": value, "unit": "Mqueries/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -693,6 +748,7 @@ def run_gpu(args):
         "shampoo": shampoo,
         "precision": precision,
         "paths": paths,
+        "small_config": small,
         "roofline": {"kernel": "k_infer_tc (fused encode + 6 tcgen05 layers)", "bound": "tensor", "achieved": achieved,
                      "peak": burst, "unit": "TFLOP/s", "frac": achieved / burst, "traffic": infer_traffic(),
                      "peak_source": f"{src} bf16 dense burst (fp16 peak = bf16 peak)"},
