@@ -336,16 +336,13 @@ cudaError_t launch_shampoo(Cache* c, int n_partials, float grad_scale, float* lo
   cudaError_t e = cudaLaunchKernelEx(&lc, k_shampoo_grad, (const float*)c->partials, n_partials, net, grad_scale, (const long long*)c->t, c->sh_g, c->m, c->v, c->sh_anorm, k.beta1,
                                      k.beta2, k.adam_eps, loss_out);
   if (e != cudaSuccess) return e;
-  static bool attr_done = false;
+  static std::atomic<int> attr_done[4];
   const int smem_roots = 5 * kShN * kShN * 4, smem_update = 4 * kShN * kShN * 4;
-  if (!attr_done) {
-    e = cudaFuncSetAttribute(k_shampoo_roots, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_roots);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_shampoo_update<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_update);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_shampoo_update<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_update);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_shampoo_update<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_update);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
+  e = ensure_smem(k_shampoo_roots, smem_roots, &attr_done[0]);
+  if (e == cudaSuccess) e = ensure_smem(k_shampoo_update<0>, smem_update, &attr_done[1]);
+  if (e == cudaSuccess) e = ensure_smem(k_shampoo_update<1>, smem_update, &attr_done[2]);
+  if (e == cudaSuccess) e = ensure_smem(k_shampoo_update<2>, smem_update, &attr_done[3]);
+  if (e != cudaSuccess) return e;
   k_shampoo_roots<<<2 * net.n_mats, kShThreads, smem_roots, st>>>(net, c->sh_g, c->sh_stats, c->sh_roots,
                                                                   (const long long*)c->t, k.beta2, k.shampoo_eps,
                                                                   k.shampoo_interval);

@@ -164,15 +164,11 @@ __global__ void __launch_bounds__(128) k_infer_simt(const float* __restrict__ re
 
 cudaError_t launch_infer_simt(Cache* c, const float* rec, int64_t n, float* rgb, cudaStream_t st) {
   const size_t smem = size_t(c->net.n_params) * 4;
-  static bool attr_set[2] = {false, false};
+  static std::atomic<int> attr_done[2];
   const int mode = c->cfg.enc_mode;
-  cudaError_t e = cudaSuccess;
-  if (!attr_set[mode]) {
-    e = mode == 0 ? cudaFuncSetAttribute(k_infer_simt<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem))
-                  : cudaFuncSetAttribute(k_infer_simt<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
-    attr_set[mode] = true;
-  }
+  cudaError_t e = mode == 0 ? ensure_smem(k_infer_simt<0>, int(smem), &attr_done[0])
+                            : ensure_smem(k_infer_simt<1>, int(smem), &attr_done[1]);
+  if (e != cudaSuccess) return e;
   const int64_t want = (n + 127) / 128;
   const int64_t cap = int64_t(c->sm_count) * 2;
   const unsigned blocks = unsigned(want < cap ? want : cap);
@@ -385,14 +381,12 @@ size_t train_simt_smem(const NetShape& net) {
 cudaError_t launch_train_simt(Cache* c, const float* pool, const float* target, int64_t n_pool, int64_t batch,
                               uint64_t a, uint64_t cc, int step, int* n_partials, cudaStream_t st) {
   const size_t smem = train_simt_smem(c->net);
-  static bool attr_set[2] = {false, false};
+  static std::atomic<int> attr_done[2];
   const int mode = c->cfg.enc_mode;
-  if (!attr_set[mode]) {
-    cudaError_t e =
-        mode == 0 ? cudaFuncSetAttribute(k_train_simt<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem))
-                  : cudaFuncSetAttribute(k_train_simt<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  {
+    const cudaError_t e = mode == 0 ? ensure_smem(k_train_simt<0>, int(smem), &attr_done[0])
+                                    : ensure_smem(k_train_simt<1>, int(smem), &attr_done[1]);
     if (e != cudaSuccess) return e;
-    attr_set[mode] = true;
   }
   const int blocks = int((batch + kTrainRows - 1) / kTrainRows);
   cudaError_t pe = ensure_partials(c, blocks);

@@ -572,17 +572,6 @@ cudaError_t launch_wait_probe(int* err, unsigned long long limit_ns, cudaStream_
   return cudaGetLastError();
 }
 
-// Raises a kernel's dynamic shared-memory limit once per process (the
-// attribute is per function; repeating the call on every launch costs
-// host time on the launch path).  `done` is per kernel instance.
-template <typename K>
-static cudaError_t set_smem(K kernel, int bytes, int* done) {
-  if (*done >= bytes) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess) *done = bytes;
-  return e;
-}
-
 cudaError_t launch_infer_tc(Cache* c, const float* rec, int64_t n, float* rgb, cudaStream_t st, const uint8_t* image) {
   InferParams p;
   p.rec = rec;
@@ -602,9 +591,9 @@ cudaError_t launch_infer_tc(Cache* c, const float* rec, int64_t n, float* rgb, c
   const bool bf16 = c->cfg.dtype == NRC_BF16;
   const int mode = c->cfg.enc_mode;
   cudaError_t e;
-  static int attr_done[4] = {0, 0, 0, 0};
+  static std::atomic<int> attr_done[4];
 #define NRC_LAUNCH(M, B)                                                   \
-  e = set_smem(k_infer_tc<M, B>, smem, &attr_done[2 * (M) + ((B) ? 1 : 0)]); \
+  e = ensure_smem(k_infer_tc<M, B>, smem, &attr_done[2 * (M) + ((B) ? 1 : 0)]); \
   if (e != cudaSuccess) return e;                                          \
   k_infer_tc<M, B><<<grid, kInferThreads, smem, st>>>(p);
   if (mode == 0 && !bf16) {
@@ -638,9 +627,9 @@ cudaError_t launch_infer_batched(const Cache* proto, const BatchCache* caches, c
   const int mode = proto->cfg.enc_mode;
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
-  static int attr_done[4] = {0, 0, 0, 0};
+  static std::atomic<int> attr_done[4];
 #define NRC_LAUNCH(M, B)                                                        \
-  e = set_smem(k_infer_batched<M, B>, smem, &attr_done[2 * (M) + ((B) ? 1 : 0)]); \
+  e = ensure_smem(k_infer_batched<M, B>, smem, &attr_done[2 * (M) + ((B) ? 1 : 0)]); \
   if (e != cudaSuccess) return e;                                               \
   k_infer_batched<M, B><<<unsigned(grid), kInferThreads, smem, st>>>(p);
   if (mode == 0 && !bf16) {
@@ -1065,7 +1054,7 @@ cudaError_t launch_train_tc(Cache* c, const float* pool, const float* target, in
   const int smem = ((p.img_bytes + 1023) & ~1023) + p.n_mats * 16384 + 2 * 16384 + 1024;
   const bool bf16 = c->cfg.dtype == NRC_BF16;
   const int mode = c->cfg.enc_mode;
-  static int attr_done[4] = {0, 0, 0, 0};
+  static std::atomic<int> attr_done[4];
   cudaLaunchConfig_t lc = {};
   lc.gridDim = dim3(unsigned(grid));
   lc.blockDim = dim3(kTrainThreads);
@@ -1077,7 +1066,7 @@ cudaError_t launch_train_tc(Cache* c, const float* pool, const float* target, in
   lc.attrs = attr;
   lc.numAttrs = 1;
 #define NRC_LAUNCH(M, B)                                                   \
-  e = set_smem(k_train_tc<M, B>, smem, &attr_done[2 * (M) + ((B) ? 1 : 0)]); \
+  e = ensure_smem(k_train_tc<M, B>, smem, &attr_done[2 * (M) + ((B) ? 1 : 0)]); \
   if (e != cudaSuccess) return e;                                          \
   e = cudaLaunchKernelEx(&lc, k_train_tc<M, B>, p);                        \
   if (e != cudaSuccess) return e;
@@ -1128,9 +1117,9 @@ cudaError_t launch_train_batched(const Cache* proto, const TrainJob* jobs, int n
   lc.attrs = attr;
   lc.numAttrs = 1;
   cudaError_t e = cudaSuccess;
-  static int attr_done[4] = {0, 0, 0, 0};
+  static std::atomic<int> attr_done[4];
 #define NRC_LAUNCH(M, B)                                                   \
-  e = set_smem(k_train_tc<M, B>, smem, &attr_done[2 * (M) + ((B) ? 1 : 0)]); \
+  e = ensure_smem(k_train_tc<M, B>, smem, &attr_done[2 * (M) + ((B) ? 1 : 0)]); \
   if (e != cudaSuccess) return e;                                          \
   e = cudaLaunchKernelEx(&lc, k_train_tc<M, B>, p);                        \
   if (e != cudaSuccess) return e;
@@ -1179,14 +1168,14 @@ cudaError_t launch_infer_fp8(Cache* c, const float* rec, int64_t n, float* rgb, 
   const int64_t n_tiles = (n + kTile - 1) / kTile;
   const int64_t want = (n_tiles + kSlots - 1) / kSlots;
   const unsigned grid = unsigned(want < c->sm_count ? want : c->sm_count);
-  static int attr_done[2] = {0, 0};
+  static std::atomic<int> attr_done[2];
   cudaError_t e;
   if (c->cfg.enc_mode == 0) {
-    e = set_smem(k_infer_fp8<0>, smem, &attr_done[0]);
+    e = ensure_smem(k_infer_fp8<0>, smem, &attr_done[0]);
     if (e != cudaSuccess) return e;
     k_infer_fp8<0><<<grid, kInferThreads, smem, st>>>(p);
   } else {
-    e = set_smem(k_infer_fp8<1>, smem, &attr_done[1]);
+    e = ensure_smem(k_infer_fp8<1>, smem, &attr_done[1]);
     if (e != cudaSuccess) return e;
     k_infer_fp8<1><<<grid, kInferThreads, smem, st>>>(p);
   }

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "nrc.h"
 
 namespace nrc {
@@ -28,6 +30,21 @@ constexpr unsigned long long kWaitLimitNs = 2000000000ull;
 // the device were out of memory.
 extern int g_alloc_skip, g_alloc_fail;
 cudaError_t dev_alloc_bytes(void** p, size_t bytes);
+// Raises a kernel's dynamic shared-memory limit to at least `bytes`.  `done`
+// (one per kernel instance) remembers the largest limit set so far, so that
+// the attribute is set once per increase, never lowered, and concurrent first
+// launches from several host threads are safe.
+template <typename K>
+inline cudaError_t ensure_smem(K kernel, int bytes, std::atomic<int>* done) {
+  if (done->load(std::memory_order_acquire) >= bytes) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  int cur = done->load(std::memory_order_relaxed);
+  while (cur < bytes && !done->compare_exchange_weak(cur, bytes, std::memory_order_acq_rel)) {
+  }
+  return cudaSuccess;
+}
+
 // Every device allocation of the library goes through here.
 template <class T>
 inline cudaError_t dev_alloc(T** p, size_t bytes) {
