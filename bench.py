@@ -204,8 +204,8 @@ def run_reference(args):
     values = []
     descs = []
     cores = 1
-    # about 90 s of oracle work in all, however many steps are asked for
-    per = max(0.05, 90.0 / max(1, args.steps + args.warmup))
+    # about args.ref_seconds (90 s) of oracle work in all, however many steps are asked for
+    per = max(0.05, args.ref_seconds / max(1, args.steps + args.warmup))
     for i in range(args.warmup + args.steps):
         v, d, cores, _ = cpu_oracle_frame(per)
         if i >= args.warmup:
@@ -773,6 +773,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched-caches and serving measurements")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--ref-seconds", type=float, default=90.0, help="oracle work of the whole --impl reference run")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
