@@ -489,7 +489,10 @@ NRC_API int32_t nrc_paths_adapt_tile(int32_t tile, int64_t generated, int64_t ta
  * light along the path, throughput-weighted), render_throughput [pixels][3]
  * (throughput from the camera to the terminal vertex), tiles [n_tiles][4]
  * int32 {pixel or -1, n, m, unbiased} and tail_queries [n_tiles][16] (the
- * record of x_m, the training path's self-training query). */
+ * record of x_m, the training path's self-training query; rows of tiles
+ * without a training path are left as they are).  tail_queries may be
+ * render_queries + 16 * pixels, so that one nrc_infer over pixels + n_tiles
+ * records answers both.  Record and tile buffers must be 16-byte aligned. */
 NRC_API nrc_status nrc_paths_terminate(const nrc_paths* paths, const nrc_path_params* params,
                                        float* render_queries, float* render_emitted, float* render_throughput,
                                        int32_t* tiles, float* tail_queries, nrc_stream stream);
