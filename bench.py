@@ -628,7 +628,12 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
     from paper_2106_12372_gb300 import build
 
+    # one process compiles (if the library is stale); the other ranks then find it built
+    if ws > 1 and rank != 0:
+        torch.distributed.barrier()
     build.build()
+    if ws > 1 and rank == 0:
+        torch.distributed.barrier()
     stream = torch.cuda.current_stream()
 
     seed = 2106 + rank
