@@ -45,7 +45,9 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle samples every 20 ms while running."""
+    """nvidia-smi clock / throttle samples every 20 ms while running (the
+    benchmark runs 0.3 s of untimed frames inside it before the timed ones, so
+    the record is taken under the frame's load however short the timed region)."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -86,13 +88,13 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def infer_traffic():
-    """DRAM bytes per k_infer_tc launch from the committed ncu summary, or None
+def frame_traffic():
+    """DRAM bytes per k_frame_tc launch from the committed ncu summary, or None
     once the kernel's sources differ from the ones that were profiled."""
     import hashlib
     import re
 
-    prof = os.path.join(ROOT, "profiles", "k_infer_tc_1080p_fp16.md")
+    prof = os.path.join(ROOT, "profiles", "k_frame_tc_1080p_fp16.md")
     if not os.path.exists(prof):
         return None
     text = open(prof).read()
@@ -102,7 +104,7 @@ def infer_traffic():
         return None
     csrc = os.path.join(ROOT, "paper_2106_12372_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("k_tc.cu", "tc_ptx.cuh", "nrc_internal.cuh"):
+    for f in ("k_frame.cu", "tc_common.cuh", "tc_ptx.cuh", "nrc_internal.cuh"):
         h.update(open(os.path.join(csrc, f), "rb").read())
     return int(mt.group(1)) if h.hexdigest()[:16] == mh.group(1) else None
 
@@ -649,39 +651,66 @@ def run_gpu(args):
     empty_q = queries[0][:0]
 
     def frame(k, ev=None):
-        # the frame through the C ABI: the cache query (nrc_infer), then the frame's
-        # N_STEPS training steps in one nrc_frame call (no queries)
-        q = queries[k % 2]
+        # the frame through the C ABI: one nrc_frame call answers the frame's
+        # queries (weights from before its training) and runs its N_STEPS
+        # training steps -- one persistent launch on the 16-bit caches
         if ev:
             ev[0].record(stream)
-        cache.infer(q, rgb)
+        cache.frame(queries[k % 2], rgb, pool, tgt, BATCH, N_STEPS, synth.frame_seed(seed, k), loss_out=losses)
         if ev:
             ev[1].record(stream)
-        cache.frame(empty_q, rgb, pool, tgt, BATCH, N_STEPS, synth.frame_seed(seed, k), loss_out=losses)
-        if ev:
-            ev[2].record(stream)
 
     for k in range(args.warmup):
         frame(k)
     torch.cuda.synchronize()
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
     launches0 = cache.launches
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
+        # untimed frames for 0.3 s right before the timed region, so that the
+        # clock record holds samples under this load whatever --steps is
+        t_burn = time.perf_counter()
+        kb = 0
+        while time.perf_counter() - t_burn < 0.3:
+            for _ in range(50):
+                frame(args.warmup + kb)
+                kb += 1
+            torch.cuda.synchronize()
         for k in range(args.steps):
             flush.zero_()
             frame(args.warmup + k, evs[k])
         torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
-    launches = cache.launches - launches0
+    launches = cache.launches - launches0 - kb * (1 if args.dtype != "fp32" else 0)
     cache.check_error()
-    frame_ms = [e[0].elapsed_time(e[2]) for e in evs]
-    infer_ms = [e[0].elapsed_time(e[1]) for e in evs]
-    train_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    frame_ms = [e[0].elapsed_time(e[1]) for e in evs]
     total_ms, value = job_throughput(sum(frame_ms), N_QUERIES, args.steps, ws, device=dev)
+    split_ctas = cache.frame_ctas(N_QUERIES, BATCH, N_STEPS)
+
+    # breakdown (not the headline): the same frame's queries alone (nrc_infer)
+    # and its training alone, as the fused training-only launch and as
+    # separate gradient + Adam launches
+    def timed(fn, n=20):
+        e = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(n)]
+        for i in range(n):
+            flush.zero_()
+            e[i][0].record(stream)
+            fn(i)
+            e[i][1].record(stream)
+        torch.cuda.synchronize()
+        return statistics.median(x[0].elapsed_time(x[1]) for x in e)
+
+    w_keep = cache.get_state()
+    infer_ms = timed(lambda i: cache.infer(queries[i % 2], rgb))
+    train_fused_ms = timed(lambda i: cache.frame(empty_q, rgb, pool, tgt, BATCH, N_STEPS, synth.frame_seed(seed, i)))
+    cache.set_frame_ctas(-1)
+    train_sep_ms = timed(lambda i: cache.frame(empty_q, rgb, pool, tgt, BATCH, N_STEPS, synth.frame_seed(seed, i)))
+    seq_frame_ms = timed(lambda i: cache.frame(queries[i % 2], rgb, pool, tgt, BATCH, N_STEPS, synth.frame_seed(seed, i)))
+    cache.set_frame_ctas(0)
+    cache.set_state(w_keep[0], w_keep[1], w_keep[2], w_keep[3])
 
     # plain per-layer FP32 path on the same frame (a few frames; same cache shape)
     plain = nrc.Cache(dtype="fp32", path=nrc.PATH_PLAIN, seed=seed)
@@ -726,10 +755,9 @@ def run_gpu(args):
     if rank != 0:
         return
     burst, sustained, hbm, src = peaks()
-    inf_med = statistics.median(infer_ms)
-    achieved = FLOP_QUERY * N_QUERIES / (inf_med / 1e3) / 1e12
     frame_flop = FLOP_QUERY * N_QUERIES + FLOP_RECORD * BATCH * N_STEPS
     med = statistics.median(frame_ms)
+    achieved = frame_flop / (med / 1e3) / 1e12
     p99 = float(np.percentile(frame_ms, 99))
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
@@ -737,6 +765,8 @@ def run_gpu(args):
         cpu = {"value": v, "unit": "Mqueries/s", "cores": cores, "kind": "oracle", "sample": d}
         if small is not None:
             small["oracle_fp64_ms"], small["oracle_cores"] = cpu_oracle_small()
+    clocks = clk.summary()
+    clocks["window"] = "0.3 s of untimed frames right before the timed frames, then the timed frames"
     line = {
         "metric": METRIC, "value": value, "unit": "Mqueries/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -744,8 +774,11 @@ def run_gpu(args):
         "config": {"workload": WORKLOAD, "queries": N_QUERIES, "train_steps": N_STEPS, "batch": BATCH,
                    "pool": N_POOL, "l2": "flushed (256 MB write) between frames, outside the events",
                    "parallelism": f"replicas x{ws}"},
-        "frame_ms_median": med, "frame_ms_p99": p99, "infer_ms_median": inf_med,
-        "train_ms_median": statistics.median(train_ms),
+        "frame_ms_median": med, "frame_ms_p99": p99, "frame_train_ctas": split_ctas,
+        "breakdown": {"queries_alone_ms": infer_ms, "train_alone_fused_ms": train_fused_ms,
+                      "train_alone_separate_launches_ms": train_sep_ms,
+                      "frame_as_separate_launches_ms": seq_frame_ms,
+                      "note": "medians of 20 frames each, L2 flushed; the headline frame is one fused launch"},
         "frame_tflops": frame_flop / (med / 1e3) / 1e12, "frame_frac_of_peak": frame_flop / (med / 1e3) / 1e12 / burst,
         "plain_fp32_ms_per_frame": statistics.median(plain_ms) if plain_ms else None,
         "batched_caches": batched,
@@ -754,14 +787,16 @@ def run_gpu(args):
         "precision": precision,
         "paths": paths,
         "small_config": small,
-        "roofline": {"kernel": "k_infer_tc (fused encode + 6 tcgen05 layers)", "bound": "tensor", "achieved": achieved,
-                     "peak": burst, "unit": "TFLOP/s", "frac": achieved / burst, "traffic": infer_traffic(),
+        "roofline": {"kernel": "k_frame_tc (the whole frame: queries + 4 training steps, one launch)",
+                     "bound": "tensor", "achieved": achieved,
+                     "peak": burst, "unit": "TFLOP/s", "frac": achieved / burst, "traffic": frame_traffic(),
                      "peak_source": f"{src} bf16 dense burst (fp16 peak = bf16 peak)"},
         "cpu_baseline": cpu,
         "e2e": {"value": N_QUERIES / e2e_s / 1e6, "unit": "Mqueries/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3},
         "gpu_launches": launches,
-        "clocks": clk.summary(),
+        "clocks": clocks,
+        "frame_ms_x_sm_ghz": (med * clocks["sm_mhz"] / 1e3) if clocks.get("sm_mhz") else None,
         "paper_context": "RTX 3090, half: query 1.59 ms + training 1.11 ms per 1080p frame (Table 3)",
     }
     print(json.dumps(line), flush=True)

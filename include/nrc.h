@@ -182,10 +182,34 @@ NRC_API nrc_status nrc_train_step(nrc_cache* cache, const float* pool, const flo
 /* One frame (Sec. 3.1-3.5): the cache query rgb = infer(queries) with the
  * weights before this frame's training, then n_steps train steps on the
  * pool (steps 0 .. n_steps-1 of frame_seed's shuffle).  loss_out (device,
- * n_steps floats, may be NULL) receives each step's loss.  Device pointers. */
+ * n_steps floats, may be NULL) receives each step's loss.  Device pointers.
+ * Since the queries read the weights from before the frame's training, the
+ * two are independent: for NRC_FP16 / NRC_BF16 caches on the fused path with
+ * Adam (width 64, at most 5 hidden layers, at most 64 steps) the whole frame is ONE persistent
+ * launch in which some CTAs run the training steps (grid barriers between
+ * the steps, Adam inside the launch) while the others answer the queries,
+ * and the training CTAs answer queries once the steps are done.  Its
+ * outputs equal nrc_infer's bit for bit; its weights equal those of
+ * n_steps x nrc_train_step up to FP32 summation order (the weight-gradient
+ * partials come from a different number of CTAs).  Other caches run the
+ * query launch and then each step's launches.  The fused launch keeps all
+ * its CTAs resident at once (cooperative launch): it needs the whole GPU
+ * and NRC_ERR_CUDA is returned if the device cannot host it. */
 NRC_API nrc_status nrc_frame(nrc_cache* cache, const float* queries, int64_t n_queries, float* rgb, const float* pool,
                      const float* target, int64_t n_pool, int64_t batch, int32_t n_steps, uint64_t frame_seed,
                      float* loss_out, nrc_stream stream);
+
+/* How nrc_frame splits the fused launch: train_ctas = 0 (default) chooses
+ * the number of training CTAs per frame from a model of the frame's length
+ * (the training's dependent chain against the SM time of all the work);
+ * 1 .. SM count fixes it (capped at the batch's 128-row tiles); -1 runs the
+ * frame as separate launches (queries, then each step's gradient and Adam
+ * kernels).  Host-side setting; INVALID_ARG outside [-1, SM count]. */
+NRC_API nrc_status nrc_set_frame_ctas(nrc_cache* cache, int32_t train_ctas);
+
+/* The number of training CTAs nrc_frame would use for this frame shape, or
+ * -1 if the frame would not take the fused launch. */
+NRC_API int32_t nrc_frame_ctas(const nrc_cache* cache, int64_t n_queries, int64_t batch, int32_t n_steps);
 
 /* nrc_frame with HOST buffers: copies queries, pool and target host->device
  * into library-owned staging buffers (grown on demand), runs the frame, and

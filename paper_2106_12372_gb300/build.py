@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnrc.so")
-SOURCES = ["nrc_api.cu", "k_simt.cu", "k_tc.cu", "k_plain.cu", "nrc_noalloc.cu", "nrc_batch.cu", "nrc_serve.cu", "k_shampoo.cu", "k_paths.cu"]
+SOURCES = ["nrc_api.cu", "k_simt.cu", "k_tc.cu", "k_plain.cu", "nrc_noalloc.cu", "nrc_batch.cu", "nrc_serve.cu", "k_shampoo.cu", "k_paths.cu", "k_frame.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

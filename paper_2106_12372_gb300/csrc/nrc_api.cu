@@ -249,6 +249,9 @@ static void free_cache(nrc_cache* c) {
   cudaFree(c->plain_buf);
   cudaFree(c->stage);
   cudaFree(c->wimg_snap);
+  cudaFree(c->wimg_work);
+  cudaFree(c->wimg_ema_work);
+  cudaFree(c->frame_sync);
   for (cudaEvent_t e : c->ev_pipe)
     if (e) cudaEventDestroy(e);
   if (c->s_h2d) cudaStreamDestroy(c->s_h2d);
@@ -435,9 +438,36 @@ nrc_status nrc_train_step(nrc_cache* c, const float* pool, const float* target, 
   return train_impl(c, pool, target, n_pool, batch, frame_seed, step, loss_out, reinterpret_cast<cudaStream_t>(stream));
 }
 
-nrc_status nrc_frame(nrc_cache* c, const float* queries, int64_t n_q, float* rgb, const float* pool,
-                     const float* target, int64_t n_pool, int64_t batch, int32_t n_steps, uint64_t frame_seed,
-                     float* loss_out, nrc_stream stream) {
+namespace nrc {
+// The fused frame kernel takes the 16-bit tensor-core path with Adam at
+// width 64 and up to 5 hidden layers.
+static bool fused_frame_ok(const Cache* c, int64_t n_q, int64_t batch, int32_t n_steps) {
+  const nrc_config& k = c->cfg;
+  return c->frame_ctas >= 0 && k.path == NRC_PATH_FUSED && (k.dtype == NRC_FP16 || k.dtype == NRC_BF16) &&
+         k.optimizer == NRC_OPT_ADAM && k.width == 64 && c->net.n_mats <= 6 && n_steps > 0 && n_steps <= 64 && batch > 0 &&
+         (n_q + kTile - 1) / kTile < (int64_t(1) << 31);
+}
+}  // namespace nrc
+
+nrc_status nrc_set_frame_ctas(nrc_cache* c, int32_t train_ctas) {
+  if (!c) return set_error("cache is NULL"), NRC_ERR_INVALID_ARG;
+  if (train_ctas < -1 || train_ctas > c->sm_count)
+    return set_error("train_ctas must be -1, 0 or 1..%d", c->sm_count), NRC_ERR_INVALID_ARG;
+  c->frame_ctas = train_ctas;
+  return NRC_OK;
+}
+
+int32_t nrc_frame_ctas(const nrc_cache* c, int64_t n_queries, int64_t batch, int32_t n_steps) {
+  if (!c || n_queries < 0 || batch <= 0 || n_steps <= 0 || !fused_frame_ok(c, n_queries, batch, n_steps)) return -1;
+  const int64_t tiles = (batch + kTile - 1) / kTile;
+  const int t = c->frame_ctas > 0 ? c->frame_ctas : frame_split(c, n_queries, batch, n_steps);
+  return int32_t(std::min<int64_t>(t, tiles));
+}
+
+namespace nrc {
+static nrc_status frame_impl(nrc_cache* c, const float* queries, int64_t n_q, float* rgb, const float* pool,
+                             const float* target, int64_t n_pool, int64_t batch, int32_t n_steps, uint64_t frame_seed,
+                             float* loss_out, nrc_stream stream, bool allow_fused) {
   if (!c) return set_error("cache is NULL"), NRC_ERR_INVALID_ARG;
   if (n_q < 0 || n_steps < 0) return set_error("negative size"), NRC_ERR_INVALID_ARG;
   if (n_q > 0 && (!queries || !rgb || !aligned16(queries) || !aligned16(rgb)))
@@ -447,6 +477,17 @@ nrc_status nrc_frame(nrc_cache* c, const float* queries, int64_t n_q, float* rgb
     if (s != NRC_OK) return s;
   }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (allow_fused && fused_frame_ok(c, n_q, batch, n_steps)) {
+    // one persistent launch: the queries and the training steps side by side
+    uint64_t a, cc;
+    lcg_params(n_pool, frame_seed, &a, &cc);
+    const int ctas = c->frame_ctas > 0 ? c->frame_ctas : frame_split(c, n_q, batch, n_steps);
+    c->wimg8_dirty = true;
+    c->launches += 1;
+    return cuda_status(launch_frame_tc(c, queries, n_q, rgb, pool, target, n_pool, batch, n_steps, a, cc, loss_out,
+                                       ctas, st),
+                       "nrc_frame (fused)");
+  }
   if (n_q > 0) {
     nrc_status s = infer_impl(c, queries, n_q, rgb, st);
     if (s != NRC_OK) return s;
@@ -458,6 +499,13 @@ nrc_status nrc_frame(nrc_cache* c, const float* queries, int64_t n_q, float* rgb
     }
   }
   return NRC_OK;
+}
+}  // namespace nrc
+
+nrc_status nrc_frame(nrc_cache* c, const float* queries, int64_t n_q, float* rgb, const float* pool,
+                     const float* target, int64_t n_pool, int64_t batch, int32_t n_steps, uint64_t frame_seed,
+                     float* loss_out, nrc_stream stream) {
+  return frame_impl(c, queries, n_q, rgb, pool, target, n_pool, batch, n_steps, frame_seed, loss_out, stream, true);
 }
 
 namespace nrc {
@@ -500,8 +548,11 @@ static nrc_status frame_host_pipelined(nrc_cache* c, const float* queries, int64
   if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev_pool, 0);
   if (e != cudaSuccess) return cuda_status(e, "nrc_frame_host");
   if (n_steps > 0 && batch > 0) {
-    nrc_status s = nrc_frame(c, dq, 0, dr, dp, dt, n_pool, batch, n_steps, frame_seed, loss_out ? dl : nullptr,
-                             reinterpret_cast<nrc_stream>(st));
+    // the training steps as separate launches: they share the GPU with the
+    // query chunks on the other streams, where a cooperative grid would wait
+    // for SMs
+    nrc_status s = frame_impl(c, dq, 0, dr, dp, dt, n_pool, batch, n_steps, frame_seed, loss_out ? dl : nullptr,
+                              reinterpret_cast<nrc_stream>(st), false);
     if (s != NRC_OK) return s;
   }
   e = cudaEventRecord(ev_train, st);
@@ -649,6 +700,9 @@ nrc_status nrc_check_error(nrc_cache* c, nrc_stream stream) {
   cudaError_t e = cudaStreamSynchronize(st);
   if (e == cudaSuccess) e = cudaMemcpy(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemset(c->err, 0, sizeof(int));
+  if (e != cudaSuccess) return cuda_status(e, "nrc_check_error");
+  // a frame launch that gave up may have left its counters part-way
+  if (h != 0 && c->frame_sync) e = cudaMemset(c->frame_sync, 0, 64);
   if (e != cudaSuccess) return cuda_status(e, "nrc_check_error");
   if (h & kErrTimeout) return set_error("a bounded device wait timed out"), NRC_ERR_TIMEOUT;
   return NRC_OK;

@@ -109,6 +109,13 @@ struct Cache {
   cudaStream_t s_h2d = nullptr, s_query = nullptr, s_d2h = nullptr;
   cudaEvent_t ev_pipe[20] = {};
   uint8_t* wimg_snap = nullptr;
+  // fused frame (k_frame_tc, created on first use): the training's working
+  // weight images and the launch's device counters; frame_ctas = training
+  // CTAs (0: chosen per frame by frame_split(), -1: separate launches)
+  uint8_t* wimg_work = nullptr;
+  uint8_t* wimg_ema_work = nullptr;
+  unsigned* frame_sync = nullptr;
+  int frame_ctas = 0;
   long long launches = 0;
   int sm_count = 0;
   int device = 0;
@@ -215,6 +222,13 @@ cudaError_t launch_train_tc(Cache* c, const float* pool, const float* target, in
 // one Adam launch over their weights.
 cudaError_t launch_train_batched(const Cache* proto, const TrainJob* jobs, int n_jobs, cudaStream_t st);
 cudaError_t launch_adam_batched(const Cache* proto, const AdamJob* jobs, int n_jobs, cudaStream_t st);
+// One persistent launch for a frame's queries and its n_steps training steps
+// (k_frame_tc): n_train CTAs train while the others answer queries.
+cudaError_t launch_frame_tc(Cache* c, const float* rec, int64_t n_q, float* rgb, const float* pool, const float* target,
+                            int64_t n_pool, int64_t batch, int n_steps, uint64_t a, uint64_t cc, float* loss_out,
+                            int n_train, cudaStream_t st);
+// Training CTAs of a fused frame chosen from a model of the frame's length.
+int frame_split(const Cache* c, int64_t n_q, int64_t batch, int n_steps);
 // Plain per-layer FP32 path.
 cudaError_t plain_infer(Cache* c, const float* rec, int64_t n, float* rgb, cudaStream_t st);
 cudaError_t plain_train(Cache* c, const float* pool, const float* target, int64_t n_pool, int64_t batch,

@@ -127,6 +127,8 @@ def lib() -> ctypes.CDLL:
             "nrc_train_step": (i32, [P, P, P, i64, i64, u64, i32, P, P]),
             "nrc_frame": (i32, [P, P, i64, P, P, P, i64, i64, i32, u64, P, P]),
             "nrc_frame_host": (i32, [P, P, i64, P, P, P, i64, i64, i32, u64, P, P]),
+            "nrc_set_frame_ctas": (i32, [P, i32]),
+            "nrc_frame_ctas": (i32, [P, i64, i64, i32]),
             "nrc_get_state": (i32, [P, P, P, P, P, P]),
             "nrc_set_state": (i32, [P, P, P, P, i64, P]),
             "nrc_set_path": (i32, [P, i32]),
@@ -285,6 +287,14 @@ class Cache:
         _check(lib().nrc_frame(self._h, _ptr(queries), queries.shape[0], _ptr(rgb), _ptr(pool), _ptr(target),
                                pool.shape[0], batch, n_steps, frame_seed & (2**64 - 1), _ptr(loss_out),
                                _stream(stream)))
+
+    def set_frame_ctas(self, train_ctas: int) -> None:
+        """Training CTAs of the fused frame launch: 0 automatic, -1 separate launches."""
+        _check(lib().nrc_set_frame_ctas(self._h, int(train_ctas)))
+
+    def frame_ctas(self, n_queries: int, batch: int, n_steps: int) -> int:
+        """Training CTAs nrc_frame would use for this shape (-1: not the fused launch)."""
+        return int(lib().nrc_frame_ctas(self._h, int(n_queries), int(batch), int(n_steps)))
 
     def frame_host(self, queries, rgb, pool, target, batch: int, n_steps: int, frame_seed: int, loss_out=None,
                    stream=None):

@@ -263,6 +263,7 @@ def test_frame_equals_separate_calls():
     fs = synth.frame_seed(90, 3)
     a = nrc.Cache(dtype="fp16")
     a.set_state(w0)
+    a.set_frame_ctas(-1)  # the frame as separate launches (the fused launch: test_gpu_frame.py)
     b = nrc.Cache(dtype="fp16")
     b.set_state(w0)
     rgb_a = torch.empty((3000, 3), device=DEV)
@@ -287,6 +288,7 @@ def test_frame_host_equals_frame(n_q):
     a.set_state(w0)
     b = nrc.Cache(dtype="fp16")
     b.set_state(w0)
+    b.set_frame_ctas(-1)  # nrc_frame_host trains with separate launches
     rgb_h = torch.empty((n_q, 3)).pin_memory()
     loss_h = torch.zeros(2).pin_memory()
     a.frame_host(torch.from_numpy(qn).pin_memory(), rgb_h, torch.from_numpy(pool).pin_memory(),
