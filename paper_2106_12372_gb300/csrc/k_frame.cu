@@ -92,7 +92,7 @@ struct FrameParams {
   uint8_t* img_out;          // the cache's image (img_work copied here at the end)
   uint8_t* img_ema_out;
   float* partials;           // [T][partial_stride]
-  unsigned* sync;            // [0] grid barrier, [1] query tile tickets, [2] retired CTAs
+  unsigned* sync;            // [0] grid barrier, [1] query tile tickets, [2] retired CTAs, [3] CTAs holding the old image
   NetShape net;
   ImageShape img;
   int img_bytes;
@@ -245,31 +245,36 @@ __device__ __forceinline__ void frame_train(const FrameParams& p, uint8_t* sw, u
       if (elect_one()) mbar_wait(bar_w, wph, p.err);
       __syncwarp();
       wph ^= 1u;
+      // layer 0 of tile jj: reads the producer's H_0 from shared memory
+      auto issue_layer0 = [&](int jj) {
+        const int pp = jj & 1;
+        if (elect_one()) mbar_wait(&bar_full[pp], uint32_t((jj >> 1) & 1), p.err);
+        __syncwarp();
+        const uint32_t idesc = idesc_f16(128, p.img.rows[0], BF16);
+        const uint64_t a = hk + uint64_t(hbuf(0, pp)) * kBuf, bb = wk + uint64_t(p.img.off[0] >> 4);
+        fence_after();
+        if (elect_one()) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) mma_ss(tmem, a + uint64_t(2 * k), bb + uint64_t(2 * k), idesc, k > 0 ? 1u : 0u);
+          mma_commit(bar_mma);
+        }
+        __syncwarp();
+      };
       bool first = true;
       for (int64_t i = b; i < tiles; i += T, ++j) {
         const int par = j & 1;
         const bool last_tile = i + T >= tiles;
-        if (elect_one()) mbar_wait(&bar_full[par], uint32_t((j >> 1) & 1), p.err);
-        __syncwarp();
-        for (int l = 0; l < L; ++l) {  // forward
+        if (first) issue_layer0(j);  // later tiles' layer 0 went out ahead of the previous tile's last dW
+        for (int l = 1; l < L; ++l) {  // forward: A = the activations the epilogue left in TMEM
           const uint32_t idesc = idesc_f16(128, p.img.rows[l], BF16);
-          const uint64_t a = hk + uint64_t(hbuf(l, par)) * kBuf, bb = wk + uint64_t(p.img.off[l] >> 4);
-          if (l > 0) named_sync(kBarOps, kFrameCompute + 32);
+          const uint64_t bb = wk + uint64_t(p.img.off[l] >> 4);
+          named_sync(kBarOps, kFrameCompute + 32);
           fence_after();
           if (elect_one()) {
-            // layer 0 reads the producer's H_0 from shared memory, the others
-            // the activations the epilogue left in TMEM
-            if (l == 0) {
 #pragma unroll
-              for (int k = 0; k < 4; ++k) mma_ss(tmem, a + uint64_t(2 * k), bb + uint64_t(2 * k), idesc, k > 0 ? 1u : 0u);
-            } else {
-#pragma unroll
-              for (int k = 0; k < 4; ++k)
-                mma_ts(tmem, tmem + kActCol + uint32_t(8 * k), bb + uint64_t(2 * k), idesc, k > 0 ? 1u : 0u);
-            }
+            for (int k = 0; k < 4; ++k)
+              mma_ts(tmem, tmem + kActCol + uint32_t(8 * k), bb + uint64_t(2 * k), idesc, k > 0 ? 1u : 0u);
             mma_commit(bar_mma);
-            // once these complete, so has the previous tile's dW_0: its H_0 buffer is free
-            if (l == 0 && j >= 1) mma_commit(&bar_free[(j + 1) & 1]);
           }
           __syncwarp();
         }
@@ -286,12 +291,17 @@ __device__ __forceinline__ void frame_train(const FrameParams& p, uint8_t* sw, u
           if (l + 1 < L) issue_dw(l + 1, par, first, lead);
           __syncwarp();
         }
-        named_sync(kBarOps, kFrameCompute + 32);  // stage 0: dW_1 (deferred) and dW_0
+        // stage 0: the next tile's layer 0 first (the chain goes on), then
+        // dW_1 (deferred) and dW_0; their completion frees this tile's H_0
+        // buffer (producer) and the shared copies the next tile overwrites
+        named_sync(kBarOps, kFrameCompute + 32);
+        if (!last_tile) issue_layer0(j + 1);
         fence_after();
         const bool lead = elect_one();
         issue_dw(1, par, first, lead);
         issue_dw(0, par, first, lead);
         if (lead && last_tile) mma_commit(bar_mma);
+        if (lead) mma_commit(&bar_free[par]);
         __syncwarp();
         first = false;
       }
@@ -361,6 +371,7 @@ __device__ __forceinline__ void frame_train(const FrameParams& p, uint8_t* sw, u
     for (int64_t i = b; i < tiles; i += T, ++j) {
       const int par = j & 1;
       const bool last_tile = i + T >= tiles;
+      const bool first_of_step = i == b;
 
       // ------------------------------------------------------------ forward
       float y[3] = {0.f, 0.f, 0.f};
@@ -374,6 +385,12 @@ __device__ __forceinline__ void frame_train(const FrameParams& p, uint8_t* sw, u
           tmem_st8(t_act, pk);  // the next layer's A operand
           tmem_st_wait();
           release_tmem();
+          // the previous tile's last dW MMAs (issued behind this tile's layer
+          // 0) read the buffers this tile writes from here on
+          if (l == 0 && !first_of_step) {
+            if ((tid & 31) == 0) mbar_wait(&bar_free[(j - 1) & 1], uint32_t(((j - 1) >> 1) & 1), p.err);
+            __syncwarp();
+          }
           // the copy the weight gradients (and the backward masks) read, behind the next layer's MMAs
           store_q_sw128(Hb + hbuf(l + 1, par) * 16384, r, 2 * q, pk);
           fence_proxy_async_smem();
@@ -498,6 +515,15 @@ __device__ __forceinline__ void frame_train(const FrameParams& p, uint8_t* sw, u
     if (tid == 0) P[p.net.n_params] = ((red[0] + red[1]) + (red[2] + red[3])) * p.inv3n;
     train_grid_barrier(p.sync, unsigned(2 * s + 1) * unsigned(T), p.err, tid);
 
+    // the step's loss: the T partial sums, by one warp (lane k sums partials
+    // k, k + 32, ... in order, then a fixed shuffle tree)
+    if (b == 0 && warp == kFrameCompute / 32 - 1 && p.loss_out) {
+      float sl = 0.0f;
+      for (int k = tid & 31; k < T; k += 32) sl += __ldcg(p.partials + size_t(k) * stride + p.net.n_params);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) sl += __shfl_down_sync(0xffffffffu, sl, off);
+      if ((tid & 31) == 0) p.loss_out[s] = sl;
+    }
     // ------------------------------------------------------ reduce + Adam
     // Thread (ch, qd) sums partials ch*C .. ch*C+C-1 of quad qd in order; the
     // element's thread adds the NC chunk sums in order.  With more than 128
@@ -577,15 +603,24 @@ __device__ __forceinline__ void frame_train(const FrameParams& p, uint8_t* sw, u
         adam1(g);
       }
     }
-    if (b == 0 && tid == 0 && p.loss_out) {
-      float sl = 0.0f;
-      for (int k = 0; k < T; ++k) sl += __ldcg(p.partials + size_t(k) * stride + p.net.n_params);
-      p.loss_out[s] = sl;
-    }
     fence_proxy_async_global();
     if (s + 1 < p.n_steps) train_grid_barrier(p.sync, unsigned(2 * s + 2) * unsigned(T), p.err, tid);
   }
   if (b == 0 && tid == 0) *p.t_ctr = t0 + p.n_steps;
+}
+
+// The training's weight image (and weight-average image) over the cache's:
+// all threads of the CTA.
+__device__ __forceinline__ void copy_images(const FrameParams& p) {
+  const int n16 = p.img_bytes / 16;
+  const uint4* src = reinterpret_cast<const uint4*>(p.img_work);
+  uint4* dst = reinterpret_cast<uint4*>(p.img_out);
+  for (int k = threadIdx.x; k < n16; k += kFrameThreads) dst[k] = __ldcg(src + k);
+  if (p.ema) {
+    const uint4* se = reinterpret_cast<const uint4*>(p.img_ema_work);
+    uint4* de = reinterpret_cast<uint4*>(p.img_ema_out);
+    for (int k = threadIdx.x; k < n16; k += kFrameThreads) de[k] = __ldcg(se + k);
+  }
 }
 
 template <int MODE, bool BF16>
@@ -679,6 +714,20 @@ __global__ void __launch_bounds__(kFrameThreads, 1) k_frame_tc(const __grid_cons
     int buf = 0;
     prefetch(cur, buf);
     mbar_wait(&bar_wq, 0, p.err);
+    // once every CTA holds the old image (and so every training step is
+    // done), the last of them copies the training's images over the cache's
+    fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      const unsigned old = atomicAdd(&p.sync[3], 1u);
+      s_last = old + 1 == gridDim.x && p.n_train > 0 && p.n_steps > 0;
+      if (s_last) __threadfence();
+    }
+    __syncthreads();
+    if (s_last) copy_images(p);
+    __syncthreads();
+    fence_after();
     uint32_t phase = 0;
     while (cur < n_tiles) {
       const int64_t row = cur * kTile + rit;
@@ -712,24 +761,15 @@ __global__ void __launch_bounds__(kFrameThreads, 1) k_frame_tc(const __grid_cons
   }
   __syncthreads();
   if (s_last) {
-    // every CTA is done: the training's images replace the cache's, and the
-    // counters are zero again for the next launch
-    if (p.n_train > 0 && p.n_steps > 0) {
-      const int n16 = p.img_bytes / 16;
-      const uint4* src = reinterpret_cast<const uint4*>(p.img_work);
-      uint4* dst = reinterpret_cast<uint4*>(p.img_out);
-      for (int k = tid; k < n16; k += kFrameThreads) dst[k] = __ldcg(src + k);
-      if (p.ema) {
-        const uint4* se = reinterpret_cast<const uint4*>(p.img_ema_work);
-        uint4* de = reinterpret_cast<uint4*>(p.img_ema_out);
-        for (int k = tid; k < n16; k += kFrameThreads) de[k] = __ldcg(se + k);
-      }
-    }
+    // every CTA is done: without queries the training's images replace the
+    // cache's now; the counters are zero again for the next launch
+    if (n_tiles == 0 && p.n_train > 0 && p.n_steps > 0) copy_images(p);
     __syncthreads();
     if (tid == 0) {
       p.sync[0] = 0u;
       p.sync[1] = 0u;
       p.sync[2] = 0u;
+      p.sync[3] = 0u;
       __threadfence();
     }
   }

@@ -360,15 +360,19 @@ __global__ void __launch_bounds__(kInferThreads, 1) k_infer_fp8(const __grid_con
     for (int l = 0; l < p.n_mats; ++l) {
       fence_before();
       named_sync(1 + slot, 128);
-      if (rit == 0) {
+      if (rit < 32) {
+        // the slot's first warp forms the (warp-uniform) descriptor; one elected thread issues
         fence_after();
         const uint32_t idesc = idesc_e4m3(128, p.img.rows[l]);
-        const uint32_t b0 = sw_base + uint32_t(img8_offset_of(p.img, l));
+        const uint64_t bd = sdesc_sw64(sw_base + uint32_t(img8_offset_of(p.img, l)), 512);
+        if (elect_one()) {
 #pragma unroll
-        for (int k = 0; k < 2; ++k)
-          mma_ts_f8(st.tmem + st.acc_col, st.tmem + st.act_col + uint32_t(k * 8), sdesc_sw64(b0 + uint32_t(k * 32), 512),
-                    idesc, k > 0 ? 1u : 0u);
-        mma_commit(&bar_mma[slot]);
+          for (int k = 0; k < 2; ++k)
+            mma_ts_f8(st.tmem + st.acc_col, st.tmem + st.act_col + uint32_t(k * 8), bd + uint64_t(2 * k), idesc,
+                      k > 0 ? 1u : 0u);
+          mma_commit(&bar_mma[slot]);
+        }
+        __syncwarp();
       }
       if (rit == 0) mbar_wait(&bar_mma[slot], phase, p.err);
       named_sync(1 + slot, 128);
@@ -635,10 +639,14 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(const __grid_cons
     fence_proxy_async_smem();
     fence_before();
     named_sync(1, kTrainThreads);
-    if (tid == 0) {
+    if (warp == 0) {
+      // warp 0 forms the (warp-uniform) descriptors together; one elected
+      // thread issues
       fence_after();
-      issue();
-      if (commit) mma_commit(&bar_mma);
+      const bool lead = elect_one();
+      issue(lead);
+      if (commit && lead) mma_commit(&bar_mma);
+      __syncwarp();
     }
     overlap();
     mbar_wait(&bar_mma, phase, p.err);
@@ -727,13 +735,14 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(const __grid_cons
     // ------------------------------------------------------------ forward
     float y[3] = {0.f, 0.f, 0.f};
     for (int l = 0; l < L; ++l) {
-      mma_sync_issue_wait([&]() {
+      mma_sync_issue_wait([&](bool lead) {
         const uint32_t idesc = idesc_f16(128, p.img.rows[l], BF16);
-        const uint32_t b0 = sw_base + uint32_t(p.img.off[l]);
+        const uint64_t bd = sdesc_sw128(sw_base + uint32_t(p.img.off[l]), 16, 1024);
+        if (lead) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-          mma_ts(tmem + 0, tmem + 64 + uint32_t(k * 8), sdesc_sw128(b0 + uint32_t(k * 32), 16, 1024), idesc,
-                 k > 0 ? 1u : 0u);
+          for (int k = 0; k < 4; ++k)
+            mma_ts(tmem + 0, tmem + 64 + uint32_t(k * 8), bd + uint64_t(2 * k), idesc, k > 0 ? 1u : 0u);
+        }
       });
       if (l + 1 < L) {
         uint32_t v[32];
@@ -788,27 +797,29 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(const __grid_cons
     const bool last_tile = tile + J.tile_step >= J.tile_end;
     for (int l = L - 1; l >= 0; --l) {
       const bool first_acc = first;
-      mma_stage([&]() {
+      mma_stage([&](bool lead) {
         if (l > 0) {
           // delta_l (pre-mask) = delta_{l+1} W_l: K = rows of W_l (64, or 16 for the output layer)
           const int K = p.img.rows[l];
           const uint32_t idd = idesc_f16(128, 64, BF16, false, true);
-          const uint32_t b0 = sw_base + uint32_t(p.img.off[l]);
-          for (int k = 0; k < K / 16; ++k)
-            mma_ts(tmem + 0, tmem + 64 + uint32_t(k * 8), sdesc_sw128(b0 + uint32_t(k * 2048), 1024, 1024), idd,
-                   k > 0 ? 1u : 0u);
-          mma_commit(&bar_mma);
+          const uint64_t bd = sdesc_sw128(sw_base + uint32_t(p.img.off[l]), 1024, 1024);
+          if (lead) {
+            for (int k = 0; k < K / 16; ++k)
+              mma_ts(tmem + 0, tmem + 64 + uint32_t(k * 8), bd + uint64_t(128 * k), idd, k > 0 ? 1u : 0u);
+            mma_commit(&bar_mma);
+          }
         }
         // dW_l (+)= delta_{l+1}^T H_l over this tile's 128 rows
         const uint32_t idw = idesc_f16(128, 64, BF16, true, true);
         const uint32_t dcol = tmem + 128 + uint32_t(l * 64);
-        const uint32_t hb = hs_base + uint32_t(l * 16384);
-        const uint32_t db = ds_base + uint32_t(((l + 1) & 1) * 16384);
+        const uint64_t hd = sdesc_sw128(hs_base + uint32_t(l * 16384), 1024, 1024);
+        const uint64_t dd = sdesc_sw128(ds_base + uint32_t(((l + 1) & 1) * 16384), 0, 1024);
+        if (lead) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k)
-          mma_ss(dcol, sdesc_sw128(db + uint32_t(k * 2048), 0, 1024), sdesc_sw128(hb + uint32_t(k * 2048), 1024, 1024),
-                 idw, (first_acc && k == 0) ? 0u : 1u);
-        if (l == 0) mma_commit(&bar_mma);  // the last stage waits for dW_0 as well
+          for (int k = 0; k < 8; ++k)
+            mma_ss(dcol, dd + uint64_t(128 * k), hd + uint64_t(128 * k), idw, (first_acc && k == 0) ? 0u : 1u);
+          if (l == 0) mma_commit(&bar_mma);  // the last stage waits for dW_0 as well
+        }
       }, [&]() {
         if (last_tile) {
           if (l + 2 < L) stage_dw(l + 2);  // dW_{l+2} final since the previous stage's wait
