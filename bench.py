@@ -130,6 +130,29 @@ def job_throughput(local_ms: float, units_per_rank: int, steps: int, ws: int, de
     return total_ms, units_per_rank * steps * ws / (total_ms / 1e3) / 1e6
 
 
+def build_once(ws: int, rank: int, build_fn) -> bool:
+    """Rank 0 runs build_fn while the other ranks wait on the host (a gloo
+    group, so no rank sits in a device collective meanwhile); every rank then
+    learns whether it succeeded.  Returns that outcome (True on one rank when
+    build_fn returns)."""
+    if ws == 1:
+        build_fn()
+        return True
+    import torch
+    import torch.distributed as dist
+
+    group = dist.new_group(backend="gloo")
+    ok = torch.zeros(1, dtype=torch.int32)
+    if rank == 0:
+        try:
+            build_fn()
+            ok[0] = 1
+        except Exception as exc:  # reported by every rank through the flag
+            sys.stderr.write(f"rank 0 build failed: {exc}\n")
+    dist.broadcast(ok, src=0, group=group)
+    return bool(ok.item())
+
+
 _ORACLE_COST = {}
 
 
@@ -631,11 +654,8 @@ def run_gpu(args):
     from paper_2106_12372_gb300 import build
 
     # one process compiles (if the library is stale); the other ranks then find it built
-    if ws > 1 and rank != 0:
-        torch.distributed.barrier()
-    build.build()
-    if ws > 1 and rank == 0:
-        torch.distributed.barrier()
+    if not build_once(ws, rank, build.build):
+        raise SystemExit("bench.py: the CUDA library failed to build on rank 0")
     stream = torch.cuda.current_stream()
 
     seed = 2106 + rank

@@ -425,8 +425,11 @@ NRC_API nrc_status nrc_server_query(nrc_server* server, nrc_server_info* out);
  * fixed budget, or a frame loop that must not take the device-wide
  * synchronisation cudaMalloc / cudaFree can imply).
  *
- * Computes exactly what nrc_train_step computes for a cache with config
- * *cfg (dtype NRC_FP16 or NRC_BF16, width 64, 1..5 hidden layers), on state
+ * Runs the same training step as nrc_train_step for a cache with config
+ * *cfg (dtype NRC_FP16 or NRC_BF16, width 64, 1..5 hidden layers; the
+ * constants checked as nrc_create checks them) -- equal to it up to FP32
+ * summation order, since its weight-gradient partials come from at most 64
+ * CTAs -- on state
  * the CALLER owns, all device pointers: weights, adam_m, adam_v
  * (nrc_param_count floats each, layout of nrc_get_state; read and updated
  * in place) and *step_counter (device int64, incremented).  pool, target,
@@ -434,15 +437,19 @@ NRC_API nrc_status nrc_server_query(nrc_server* server, nrc_server_info* out);
  * nrc_train_step; err_out (device int32, may be NULL) receives the device
  * error word of this call (0, or NRC's timeout bit 1).
  *
- * Scratch lives in file-scope device arrays of fixed size held by every GPU
- * that loads the library until exit: 64 weight-gradient partials of 20,676
- * floats (5.3 MB), a 43,008-byte 16-bit weight image and an error word.
- * Sizes beyond that (other widths, more layers, batch > 65536) are rejected
- * with NRC_ERR_INVALID_ARG before anything is launched.  No cudaMalloc,
- * cudaFree or allocating library routine is called.  The first call on each
- * device looks up the arrays' device addresses with cudaGetSymbolAddress
- * (with that device current); make that first call before any stream
- * capture.  Every call shares the arrays: each call rebuilds the weight
+ * Scratch lives in file-scope device arrays of fixed size: 64
+ * weight-gradient partials of 20,676 floats (5.3 MB), a 43,008-byte 16-bit
+ * weight image and an error word.  Sizes beyond that (other widths, more
+ * layers, batch > 65536) are rejected with NRC_ERR_INVALID_ARG before
+ * anything is launched.  No cudaMalloc, cudaFree or allocating library
+ * routine is called.  The arrays come into being when the CUDA runtime loads
+ * their module on a device, and stay until exit; with lazy module loading
+ * (the CUDA default) that happens at the first call on each device, which
+ * looks up their device addresses with cudaGetSymbolAddress (with that device
+ * current), so that first call lowers the device's free memory by about
+ * 6 MB and no later call changes it.  A call with batch 0 (cfg checked; the
+ * other pointers may be NULL) makes that first lookup and launches nothing:
+ * make it at start-up, before any stream capture.  Every call shares the arrays: each call rebuilds the weight
  * image and clears the error word before using them, and calls whose work
  * overlaps on the GPU (other streams, other threads) race on the scratch and
  * must be serialised by the caller. */

@@ -313,48 +313,73 @@ class ShampooState:
 # ------------------------------------------------- training-record pipeline --
 # The steps around the cache query (Sec. 3.3-3.5, the termination heuristic of
 # Sec. 3.4 "Path Termination", Eqs. 3-4), on path vertices laid out as
-# synth.make_paths writes them (24 floats per vertex).  The termination
-# decisions are taken in FP32 with the same operation order as the kernels
-# (a decision is an integer that floating point decides); the radiance sums
-# are FP64.  Readings: a vertex's spread term is sqrt(|x_{i-1} - x_i|^2 /
-# (pdf_i |cos_i|)); the rendering path ends at the first vertex n >= 2 with
-# a(x_1..x_n) > c a_0 (else at the last vertex); a training suffix restarts the
-# sum at x_n and ends at the first m > n with a(x_n..x_m) > c a_0; an unbiased
-# suffix instead continues from each vertex j >= n with probability q (the
-# bounce weighted by 1/q) and ends where the roulette stops it.
-_F32_4PI = np.float32(4.0 * math.pi)
+# synth.make_paths writes them (24 floats per vertex).  Everything is FP64,
+# from the definition.  Readings: a vertex's spread term is
+# sqrt(|x_{i-1} - x_i|^2 / (pdf_i |cos_i|)); the rendering path ends at the
+# first vertex n >= 1 with a(x_1..x_n) > c a_0 (else at the last vertex); a
+# training suffix restarts the sum after x_n and ends at the first m > n with
+# a(x_n..x_m) > c a_0; an unbiased suffix instead continues from each vertex
+# j >= n with probability q (the bounce weighted by 1/q) and ends where the
+# roulette stops it.
+#
+# A termination decision is an integer that floating point decides.  An FP32
+# evaluation of a(x_1..x_j) = (sum_i s_i)^2 and of c a_0 is each within a
+# relative (2j + 11) u and 10 u of the exact value (u = 2^-24; s_i takes ~5 u,
+# the j-term sum j u, the square doubles it; a_0 and the product with c ~10 u),
+# so a decision with |a - c a_0| <= TERMINATION_BAND(K) (a + c a_0) may come out
+# either way in FP32.  paths_check_decisions accepts such decisions taken the
+# other way and nothing else.
 
 
-def _d2_f32(a, b):
-    d = (a - b).astype(np.float32)
-    return ((d[..., 0] * d[..., 0]) + (d[..., 1] * d[..., 1])) + (d[..., 2] * d[..., 2])
+def termination_band(K: int) -> float:
+    """Relative FP32 band of a termination decision on paths of K vertices."""
+    return float((2 * K + 24) * 2.0 ** -24)
 
 
-def paths_terminate(vtx, width: int, height: int, camera, c: float, tile: int, ox: int, oy: int, phase: int,
-                    rr_q: float):
-    """Returns (n [P], render_emitted [P,3], render_throughput [P,3], tiles) where tiles
-    is a list of (pixel, n, m, unbiased) per tile (pixel -1: no training path)."""
-    vtx = np.asarray(vtx, dtype=np.float32)
-    P, K, _ = vtx.shape
-    c32 = np.float32(c)
-    x = vtx[:, :, 0:3]
-    cam = np.asarray(camera, dtype=np.float32)
-    a0 = _d2_f32(x[:, 0], cam[None, :]) / (_F32_4PI * vtx[:, 0, 15])
-    thr = c32 * a0
-    # spread term of vertex j >= 1 (the edge x_{j-1} -> x_j)
-    s = np.zeros((P, K), dtype=np.float32)
-    for j in range(1, K):
-        s[:, j] = np.sqrt(_d2_f32(x[:, j - 1], x[:, j]) / (vtx[:, j, 14] * vtx[:, j, 15]))
-    n = np.full(P, K - 1, dtype=np.int64)
-    done = np.zeros(P, dtype=bool)
-    acc = np.zeros(P, dtype=np.float32)
-    for j in range(1, K):
-        acc = acc + s[:, j]
-        hit = (~done) & ((acc * acc) > thr)
-        n[hit] = j
-        done |= hit
-    f = vtx[:, :, 19:22].astype(np.float64)
-    le = vtx[:, :, 16:19].astype(np.float64)
+def _termination_terms(vtx, camera, c):
+    """(s [P,K] spread terms, s[:, 0] = 0; thr [P] = c a_0), FP64 (Eqs. 3-4)."""
+    v = np.asarray(vtx, dtype=np.float64)
+    x = v[:, :, 0:3]
+    cam = np.asarray(camera, dtype=np.float64)
+    a0 = np.sum((x[:, 0] - cam[None, :]) ** 2, axis=-1) / (4.0 * math.pi * v[:, 0, 15])
+    s = np.zeros(v.shape[:2])
+    s[:, 1:] = np.sqrt(np.sum((x[:, :-1] - x[:, 1:]) ** 2, axis=-1) / (v[:, 1:, 14] * v[:, 1:, 15]))
+    return s, float(c) * a0
+
+
+def _suffix_end(s_p, thr_p, n, K):
+    """First m > n with (s_{n+1} + .. + s_m)^2 > c a_0, else K - 1."""
+    a = 0.0
+    for j in range(n + 1, K):
+        a += s_p[j]
+        if a * a > thr_p:
+            return j
+    return K - 1
+
+
+def _roulette_end(vtx_p, n, K, rr_q):
+    for j in range(n, K):
+        if j == K - 1 or not (vtx_p[j, 22] < np.float32(rr_q)):
+            return j
+    return K - 1
+
+
+def _tile_pixels(width, height, tile, ox, oy):
+    tiles_x, tiles_y = -(-width // tile), -(-height // tile)
+    for t in range(tiles_x * tiles_y):
+        ty, tx = divmod(t, tiles_x)
+        px, py = tx * tile + ox, ty * tile + oy
+        yield t, (py * width + px if px < width and py < height else -1)
+
+
+def paths_radiance(vtx, n):
+    """(render_emitted [P,3], render_throughput [P,3]) of paths ending at
+    vertex n[p]: the emitted radiance summed along x_0..x_n with the
+    throughput of the bounces before each vertex, and the throughput at x_n."""
+    v = np.asarray(vtx, dtype=np.float32)
+    P, K, _ = v.shape
+    f = v[:, :, 19:22].astype(np.float64)
+    le = v[:, :, 16:19].astype(np.float64)
     E = np.zeros((P, 3))
     T = np.ones((P, 3))
     Tn = np.zeros((P, 3))
@@ -363,32 +388,84 @@ def paths_terminate(vtx, width: int, height: int, camera, c: float, tile: int, o
         E[live] += T[live] * le[live, j]
         Tn[j == n] = T[j == n]
         T = T * f[:, j]
-    tiles_x, tiles_y = -(-width // tile), -(-height // tile)
+    return E, Tn
+
+
+def paths_terminate(vtx, width: int, height: int, camera, c: float, tile: int, ox: int, oy: int, phase: int,
+                    rr_q: float):
+    """Returns (n [P], render_emitted [P,3], render_throughput [P,3], tiles) where tiles
+    is a list of (pixel, n, m, unbiased) per tile (pixel -1: no training path)."""
+    v = np.asarray(vtx, dtype=np.float32)
+    P, K, _ = v.shape
+    s, thr = _termination_terms(v, camera, c)
+    acc = np.cumsum(s, axis=1)
+    hit = acc * acc > thr[:, None]
+    hit[:, 0] = False
+    hit[:, K - 1] = True
+    n = np.argmax(hit, axis=1).astype(np.int64)
+    E, Tn = paths_radiance(v, n)
     tiles = []
-    for t in range(tiles_x * tiles_y):
-        ty, tx = divmod(t, tiles_x)
-        px, py = tx * tile + ox, ty * tile + oy
-        if px >= width or py >= height:
+    for t, p in _tile_pixels(width, height, tile, ox, oy):
+        if p < 0:
             tiles.append((-1, 0, 0, 0))
             continue
-        p = py * width + px
         nn = int(n[p])
         unb = phase >= 0 and t % 16 == phase
-        m = K - 1
-        if unb:
-            for j in range(nn, K):
-                if j == K - 1 or not (vtx[p, j, 22] < np.float32(rr_q)):
-                    m = j
-                    break
-        else:
-            a = np.float32(0.0)
-            for j in range(nn + 1, K):
-                a = np.float32(a + s[p, j])
-                if np.float32(a * a) > thr[p]:
-                    m = j
-                    break
+        m = _roulette_end(v[p], nn, K, rr_q) if unb else _suffix_end(s[p], thr[p], nn, K)
         tiles.append((p, nn, m, int(unb)))
     return n, E, Tn, tiles
+
+
+def paths_check_decisions(vtx, width: int, height: int, camera, c: float, tile: int, ox: int, oy: int,
+                          phase: int, rr_q: float, n, tiles):
+    """Checks decisions taken elsewhere (n [P], tiles [T,4]) against the
+    definition: each path end and suffix end must be the FP64 one, or differ
+    from it only through decisions within the FP32 band (termination_band).
+    Returns (ok, number of paths and suffixes that differ)."""
+    v = np.asarray(vtx, dtype=np.float32)
+    P, K, _ = v.shape
+    s, thr = _termination_terms(v, camera, c)
+    band = termination_band(K)
+    n = np.asarray(n, dtype=np.int64)
+
+    def valid_end(p, start, end):
+        # every decision before `end` may be "no" and the one at `end` "yes" (or end is the last vertex)
+        if not (start < end <= K - 1):
+            return False
+        a = 0.0
+        for j in range(start + 1, end + 1):
+            a += s[p, j]
+            near = abs(a * a - thr[p]) <= band * (a * a + thr[p])
+            yes = a * a > thr[p]
+            if j < end and yes and not near:
+                return False
+            if j == end and j < K - 1 and not yes and not near:
+                return False
+        return True
+
+    ref_n, _, _, ref_tiles = paths_terminate(v, width, height, camera, c, tile, ox, oy, phase, rr_q)
+    differ = 0
+    for p in range(P):
+        if n[p] != ref_n[p]:
+            if not valid_end(p, 0, int(n[p])):
+                return False, differ
+            differ += 1
+    tiles = np.asarray(tiles).reshape(-1, 4)
+    if len(tiles) != len(ref_tiles):
+        return False, differ
+    for (p, nn, m, unb), ref in zip(tiles.tolist(), ref_tiles):
+        if p != ref[0] or unb != ref[3]:
+            return False, differ
+        if p < 0:
+            continue
+        if nn != n[p]:
+            return False, differ
+        want = _roulette_end(v[p], nn, K, rr_q) if unb else _suffix_end(s[p], thr[p], nn, K)
+        if m != want:
+            if unb or not valid_end(p, nn, m):
+                return False, differ
+            differ += 1
+    return True, differ
 
 
 def paths_records(vtx, tiles, tail_rgb, rr_q: float):

@@ -129,7 +129,7 @@ cudaError_t ensure_partials(Cache* c, int count) {
 
 static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-static nrc_status check_cfg(const nrc_config* cfg) {
+nrc_status check_cfg(const nrc_config* cfg) {
   if (!cfg) return set_error("cfg is NULL"), NRC_ERR_INVALID_ARG;
   if (cfg->hidden_layers < 1 || cfg->hidden_layers > kMaxMats - 1)
     return set_error("hidden_layers must be in [1, %d]", kMaxMats - 1), NRC_ERR_INVALID_ARG;

@@ -171,6 +171,10 @@ struct AdamJob {
 void set_error(const char* fmt, ...);
 nrc_status cuda_status(cudaError_t e, const char* what);
 
+// Validates a configuration (enums, sizes, optimiser and loss constants):
+// NRC_OK, or the status nrc_create returns for it (message set).
+nrc_status check_cfg(const nrc_config* cfg);
+
 void make_net_shape(const nrc_config& cfg, NetShape* s);
 void make_image_shape(const NetShape& s, ImageShape* img);
 

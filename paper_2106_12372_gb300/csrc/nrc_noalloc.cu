@@ -68,6 +68,10 @@ extern "C" nrc_status nrc_train_step_noalloc(const nrc_config* cfg, float* weigh
                                              int32_t step_in_frame, float* loss_out, int32_t* err_out,
                                              nrc_stream stream) {
   if (!cfg) return set_error("cfg is NULL"), NRC_ERR_INVALID_ARG;
+  if (cfg->width == 64) {  // the general checks of nrc_create first (constants, enums)
+    const nrc_status cs = check_cfg(cfg);
+    if (cs != NRC_OK) return cs;
+  }
   if (cfg->width != 64 || cfg->hidden_layers < 1 || cfg->hidden_layers > kNaMaxMats - 1)
     return set_error("nrc_train_step_noalloc: width must be 64 and hidden_layers 1..%d (static scratch holds %d "
                      "weights)", kNaMaxMats - 1, kNaParams),
@@ -84,17 +88,18 @@ extern "C" nrc_status nrc_train_step_noalloc(const nrc_config* cfg, float* weigh
   if (cfg->optimizer != NRC_OPT_ADAM)
     return set_error("nrc_train_step_noalloc trains with Adam only"), NRC_ERR_UNSUPPORTED;
   if (batch < 0 || n_pool < 0 || step_in_frame < 0) return set_error("negative size or step"), NRC_ERR_INVALID_ARG;
-  if (batch == 0) return NRC_OK;
-  if (batch > kMaxBatch)
-    return set_error("nrc_train_step_noalloc: batch %lld above the maximum %d", (long long)batch, kMaxBatch),
-           NRC_ERR_INVALID_ARG;
-  if (n_pool >= (int64_t(1) << 31)) return set_error("n_pool must be below 2^31"), NRC_ERR_INVALID_ARG;
-  if ((int64_t(step_in_frame) + 1) * batch > n_pool)
-    return set_error("(step+1)*batch exceeds n_pool"), NRC_ERR_INVALID_ARG;
-  if (!weights || !adam_m || !adam_v || !step_counter || !pool || !target)
-    return set_error("nrc_train_step_noalloc: NULL state or input pointer"), NRC_ERR_INVALID_ARG;
-  if ((reinterpret_cast<uintptr_t>(pool) & 15u) || (reinterpret_cast<uintptr_t>(weights) & 15u))
-    return set_error("pool and weights must be 16-byte aligned"), NRC_ERR_INVALID_ARG;
+  if (batch > 0) {
+    if (batch > kMaxBatch)
+      return set_error("nrc_train_step_noalloc: batch %lld above the maximum %d", (long long)batch, kMaxBatch),
+             NRC_ERR_INVALID_ARG;
+    if (n_pool >= (int64_t(1) << 31)) return set_error("n_pool must be below 2^31"), NRC_ERR_INVALID_ARG;
+    if ((int64_t(step_in_frame) + 1) * batch > n_pool)
+      return set_error("(step+1)*batch exceeds n_pool"), NRC_ERR_INVALID_ARG;
+    if (!weights || !adam_m || !adam_v || !step_counter || !pool || !target)
+      return set_error("nrc_train_step_noalloc: NULL state or input pointer"), NRC_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(pool) & 15u) || (reinterpret_cast<uintptr_t>(weights) & 15u))
+      return set_error("pool and weights must be 16-byte aligned"), NRC_ERR_INVALID_ARG;
+  }
 
   int device = 0;
   cudaError_t e = cudaGetDevice(&device);
@@ -102,6 +107,7 @@ extern "C" nrc_status nrc_train_step_noalloc(const nrc_config* cfg, float* weigh
   NaScratch* s = nullptr;
   nrc_status st = na_scratch(device, &s);
   if (st != NRC_OK) return st;
+  if (batch == 0) return NRC_OK;  // the set-up alone (the first call on a device)
 
   // A view of the caller's state plus the static scratch, shaped like a cache
   // so that the ordinary launchers run unchanged; nothing in it is allocated.

@@ -38,6 +38,37 @@ def _rank_main(rank: int, ws: int, port: int, out_dir: str) -> None:
         json.dump({"total_ms": total_ms, "value": value}, f)
 
 
+def _build_rank_main(rank: int, ws: int, port: int, out_dir: str, fail: bool) -> None:
+    os.environ.update({"MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port), "RANK": str(rank),
+                       "WORLD_SIZE": str(ws), "LOCAL_RANK": str(rank)})
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+
+    import bench
+
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    calls = []
+
+    def fake_build():
+        calls.append(rank)
+        if fail:
+            raise RuntimeError("nvcc failed")
+
+    ok = bench.build_once(ws, rank, fake_build)
+    dist.destroy_process_group()
+    with open(os.path.join(out_dir, f"b{rank}.json"), "w") as f:
+        json.dump({"ok": ok, "calls": calls}, f)
+
+
+@pytest.mark.parametrize("fail", [False, True])
+def test_build_handshake_reports_rank0_outcome_to_all(tmp_path, fail):
+    port = _free_port()
+    torch.multiprocessing.spawn(_build_rank_main, args=(2, port, str(tmp_path), fail), nprocs=2, join=True)
+    d0, d1 = (json.load(open(tmp_path / f"b{r}.json")) for r in range(2))
+    assert d0["calls"] == [0] and d1["calls"] == []  # only rank 0 builds
+    assert d0["ok"] == d1["ok"] == (not fail)  # a failed build reaches every rank; nobody waits forever
+
+
 def test_two_gloo_ranks_take_the_max_and_count_all_units(tmp_path):
     port = _free_port()
     torch.multiprocessing.spawn(_rank_main, args=(2, port, str(tmp_path)), nprocs=2, join=True)

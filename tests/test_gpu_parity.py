@@ -3,7 +3,13 @@
 Tolerances: record indexing and gather bit-exact; encoding <= 1e-6 absolute;
 outputs, loss and gradients <= 1e-5 relative (FP32 path) and <= 2e-2 (FP16 /
 BF16 tensor-core path), per output, with the relative error floored at the
-batch rms (see parity.py for why the floor is needed).
+batch rms (see parity.py for why the floor is needed).  BF16 does not meet
+2e-2 at every output: that bar is a known failure (xfail) and BF16 is held to
+it at the 99th percentile.  Every 16-bit result is also held, per element, to
+the tolerance of its format (error_bounds.format_tol: 2 |e| + 2 rms(e), e
+the error that exact FP16 / BF16 operand rounding of the oracle's arithmetic
+causes), and the GPU must sit closer to that rounding than the rounding sits
+to the FP64 result.
 """
 import numpy as np
 import pytest
@@ -11,6 +17,7 @@ import pytest
 from paper_2106_12372_gb300 import synth
 from parity import rel_err, stats
 import relu_flips as RF
+import error_bounds as EB
 
 pytestmark = pytest.mark.gpu
 
@@ -23,11 +30,25 @@ from paper_2106_12372_gb300 import nrc  # noqa: E402
 
 DEV = torch.device("cuda:0")
 DIMS = synth.layer_dims()
-TOL = {"fp32": 1e-5, "fp16": 2e-2, "bf16": 5e-2}
+TOL = {"fp32": 1e-5, "fp16": 2e-2, "bf16": 2e-2}
 # BF16 keeps 8 significant bits (FP16: 11), so its rounding error per layer is 8x larger; measured at the
-# initial weights its per-output maximum is ~3e-2 with a median of ~3e-3.  The 2e-2 bar applies to FP16 (the
-# frame's dtype) at every output and to BF16 at the 99th percentile.
+# initial weights its per-output maximum is ~3e-2 with a median of ~3e-3.  The per-output bar is asserted for
+# FP16 (the frame's dtype) everywhere and for BF16 in the xfail tests below; BF16 meets it at the 99th percentile.
 P99 = {"fp32": 1e-5, "fp16": 2e-2, "bf16": 2e-2}
+PER_OUTPUT = ("fp32", "fp16")
+MAX_FLIPS = 4  # ReLU decisions of a 16,384-record FP32 training step that may go the other way
+
+
+def format_check(got, ref, emul, dims=None, label=""):
+    """Per element |got - ref| <= format_tol(emul - ref); and rms(got - emul) <= rms(emul - ref) / 2."""
+    got, ref, emul = (np.asarray(a, np.float64).ravel() for a in (got, ref, emul))
+    e = emul - ref
+    tol = EB.format_tol(e, dims)
+    worst = float(np.max(np.abs(got - ref) / tol))
+    model = float(np.sqrt(np.mean((got - emul) ** 2)) / np.sqrt(np.mean(e ** 2)))
+    print("format bound", label, "max |err| / tol", worst, "rms(gpu - rounding) / rms(rounding error)", model)
+    assert worst <= 1.0, (label, worst)
+    assert model <= 0.5, (label, model)
 
 
 def dev(a):
@@ -90,8 +111,11 @@ def test_infer_small(dtype, n):
     got = cache.infer(dev(rec)).cpu().numpy()
     st = stats(got, ref)
     print("infer", dtype, n, st)
-    assert st["max"] <= TOL[dtype], (dtype, n, st)
+    if dtype in PER_OUTPUT:
+        assert st["max"] <= TOL[dtype], (dtype, n, st)
     assert np.quantile(rel_err(got, ref), 0.99) <= P99[dtype]
+    if dtype != "fp32" and n >= 127:
+        format_check(got, ref, EB.emulate_infer(w0, DIMS, O.encode(rec), dtype), label=f"infer {dtype} {n}")
     cache.check_error()
 
 
@@ -116,9 +140,13 @@ def test_infer_trained_weights_fp16():
     for dtype in ("fp16", "bf16"):
         cache = nrc.Cache(dtype=dtype)
         cache.set_state(w0)
-        err = rel_err(cache.infer(dev(rec)).cpu().numpy(), ref)
+        got = cache.infer(dev(rec)).cpu().numpy()
+        err = rel_err(got, ref)
         print("trained weights", dtype, err.max(), np.quantile(err, 0.99))
-        assert err.max() <= TOL[dtype] and np.quantile(err, 0.99) <= P99[dtype], (dtype, err.max())
+        assert np.quantile(err, 0.99) <= P99[dtype], (dtype, np.quantile(err, 0.99))
+        if dtype in PER_OUTPUT:
+            assert err.max() <= TOL[dtype], (dtype, err.max())
+        format_check(got, ref, EB.emulate_infer(w0, DIMS, O.encode(rec), dtype), label=f"trained weights {dtype}")
 
 
 def test_infer_full_frame_sampled():
@@ -146,6 +174,14 @@ def test_create_initialises_xavier_from_seed():
 
 
 # ------------------------------------------------------------------- train
+def _emulated_grad(dtype, n_pool, batch, step, seed, loss_mode=0):
+    """The gradient of _one_step's batch with exact 16-bit operand rounding (error_bounds.emulate_16bit)."""
+    w0 = synth.xavier_weights(DIMS, seed=seed)
+    pool, tgt = synth.make_training_pool(n_pool, seed=seed)
+    rec, tg, _ = O.gather(pool, tgt, batch, synth.frame_seed(seed, 0), step)
+    return EB.emulate_16bit(w0, DIMS, O.encode(rec), tg, dtype, per_channel=loss_mode == O.LOSS_PER_CHANNEL)[1]
+
+
 def _one_step(dtype, n_pool, batch, step, seed, loss_mode=0, mode=0):
     w0 = synth.xavier_weights(DIMS, seed=seed)
     pool, tgt = synth.make_training_pool(n_pool, seed=seed)
@@ -195,6 +231,9 @@ def test_small_config_frame_fp32(pad):
     adj, used = RF.explain(g, ref_g, flips)
     print("small config pad", pad, "ambiguous ReLU decisions", len(flips), "taken the other way", used,
           "before", stats(g, ref_g), "after", stats(g, adj))
+    # every candidate lies within twice the FP32 error bound of its 64-term sum (band 8e-6 of the magnitude
+    # sum, gamma_64 = 64 * 2^-24 = 3.8e-6); at most MAX_FLIPS of them may be taken the other way
+    assert used <= MAX_FLIPS, used
     assert rel_err(g, adj).max() <= 1e-5, stats(g, adj)
 
 
@@ -217,23 +256,44 @@ def test_train_step_16bit(dtype):
     assert abs(loss - ref_loss) <= 2e-2 * abs(ref_loss)
     g = m.astype(np.float64) / (1.0 - 0.9)
     print("train", dtype, "loss", loss, ref_loss, "grad", stats(g, ref_g))
-    assert rel_err(g, ref_g).max() <= TOL[dtype], stats(g, ref_g)
+    if dtype in PER_OUTPUT:
+        assert rel_err(g, ref_g).max() <= TOL[dtype], stats(g, ref_g)
     assert np.quantile(rel_err(g, ref_g), 0.99) <= P99[dtype]
+    format_check(g, ref_g, _emulated_grad(dtype, 65536, 16384, 3, 70), DIMS, label=f"train {dtype}")
+
+
+@pytest.mark.xfail(reason="BF16 misses the 2e-2 per-output bar at single outputs: gradient elements up to "
+                          "~4e-2 here, query outputs up to ~4e-2 in the frame test (1.7e-2 on these 4,097 "
+                          "queries); it meets the bar at the 99th percentile", strict=False)
+@pytest.mark.parametrize("what", ["infer", "train"])
+def test_bf16_per_output_bar(what):
+    if what == "infer":
+        w0 = synth.xavier_weights(DIMS, seed=40 + 4097)
+        rec = synth.make_records(4097, seed=41 + 4097)
+        cache = nrc.Cache(dtype="bf16")
+        cache.set_state(w0)
+        err = rel_err(cache.infer(dev(rec)).cpu().numpy(), O.infer(w0, DIMS, rec))
+    else:
+        ref_loss, ref_g, st, loss, w, m, v, t = _one_step("bf16", 65536, 16384, 3, 70)
+        err = rel_err(m.astype(np.float64) / (1.0 - 0.9), ref_g)
+    print("bf16 per-output", what, err.max())
+    assert err.max() <= TOL["bf16"]
 
 
 @pytest.mark.parametrize("n_pool,batch,step", [(4096, 1000, 1), (65536, 65536, 0), (2048, 128, 5)])
 def test_train_step_16bit_shapes(n_pool, batch, step):
     # ragged last tile, several tiles per CTA (dW accumulated in TMEM across tiles), a single tile.
     # FP16 rounding of weights, activations and deltas alone puts single gradient elements up to ~6e-2 of the
-    # gradient rms away from the FP64 value at a 128-row batch (the per-element bound of the 16,384-row batch,
-    # 2e-2, is tested above); the gradient as a whole must stay within 2e-2 (normwise).
+    # gradient rms away from the FP64 value at a 128-row batch, so the per-element bar here is the format's
+    # (format_check); the gradient as a whole must stay within 2e-2 (normwise).
     ref_loss, ref_g, st, loss, w, m, v, t = _one_step("fp16", n_pool, batch, step, 75 + batch)
     g = m.astype(np.float64) / (1.0 - 0.9)
     print("train fp16", n_pool, batch, "loss", loss, ref_loss, "grad", stats(g, ref_g))
     assert t == 1
     assert abs(loss - ref_loss) <= 2e-2 * abs(ref_loss)
     assert np.linalg.norm(g - ref_g) <= 2e-2 * np.linalg.norm(ref_g)
-    assert rel_err(g, ref_g).max() <= 1e-1, stats(g, ref_g)
+    format_check(g, ref_g, _emulated_grad("fp16", n_pool, batch, step, 75 + batch), DIMS,
+                 label=f"train fp16 {n_pool} {batch}")
 
 
 def test_train_steps_match_oracle_curve_fp32():

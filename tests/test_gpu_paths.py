@@ -1,9 +1,12 @@
 """GPU parity of the training-record pipeline (Sec. 3.3-3.5; termination
 heuristic Eqs. 3-4) against the oracle on seeded synthetic paths.
 
-Termination decisions, the training tiles and every record are bit-exact (both
-sides decide in FP32 in the same operation order); emitted sums, throughputs,
-targets and the composite agree to 1e-5 (FP32 against FP64, floored at the rms).
+The oracle takes the termination decisions in FP64 from the definition; the
+GPU's (FP32) must equal them except for decisions within the FP32 band of the
+threshold (oracle.paths_check_decisions), of which at most MAX_DIFFER may go
+the other way.  Given the decisions, the training tiles and every record are
+bit-exact; emitted sums, throughputs, targets and the composite agree to 1e-5
+(FP32 against FP64, floored at the rms).
 """
 import numpy as np
 import pytest
@@ -23,6 +26,24 @@ from paper_2106_12372_gb300 import build, nrc  # noqa: E402
 DEV = torch.device("cuda:0")
 DIMS = synth.layer_dims()
 W, H, K = 97, 61, 10
+MAX_DIFFER = 3
+
+
+def _ends(v, rq):
+    """The vertex index each pixel's query record was taken from (bitwise match)."""
+    rec = rq.cpu().numpy()[:, :14].view(np.uint32)
+    eq = np.all(v[:, :, :14].view(np.uint32) == rec[:, None, :], axis=2)
+    assert np.all(eq.sum(axis=1) >= 1)
+    return np.argmax(eq, axis=1)
+
+
+def _checked(v, rq, tiles, c, tile, ox, oy, phase):
+    n = _ends(v, rq)
+    t = tiles.cpu().numpy()
+    ok, differ = O.paths_check_decisions(v, W, H, synth.PATH_CAMERA, c, tile, ox, oy, phase, 0.8, n, t)
+    print("termination decisions taken the other way (within the FP32 band):", differ)
+    assert ok and differ <= MAX_DIFFER, differ
+    return n, [tuple(r) for r in t.tolist()]
 
 
 @pytest.fixture(scope="module")
@@ -46,10 +67,10 @@ def _record(vtx_row):
 def test_termination_and_tiles_match_oracle(scene, c, tile, ox, oy, phase):
     v, V = scene
     rq, em, tp, tiles, tq = nrc.paths_terminate(V, W, H, synth.PATH_CAMERA, _params(c, tile, ox, oy, phase))
-    n, E, T, ref_tiles = O.paths_terminate(v, W, H, synth.PATH_CAMERA, c, tile, ox, oy, phase, 0.8)
+    n, ref_tiles = _checked(v, rq, tiles, c, tile, ox, oy, phase)
+    E, T = O.paths_radiance(v, n)
     ref_rq = np.stack([_record(v[p, n[p]]) for p in range(W * H)])
     assert np.array_equal(rq.cpu().numpy().view(np.uint32), ref_rq.view(np.uint32))
-    assert np.array_equal(tiles.cpu().numpy(), np.array(ref_tiles, dtype=np.int32))
     tqh = tq.cpu().numpy()
     for t, (p, nn, m, unb) in enumerate(ref_tiles):
         if p >= 0:
@@ -65,8 +86,8 @@ def test_termination_and_tiles_match_oracle(scene, c, tile, ox, oy, phase):
 def test_records_and_targets_match_oracle(scene, tile, ox, oy, phase, max_records):
     v, V = scene
     prm = _params(tile=tile, ox=ox, oy=oy, phase=phase)
-    _, _, _, tiles, tq = nrc.paths_terminate(V, W, H, synth.PATH_CAMERA, prm)
-    _, _, _, ref_tiles = O.paths_terminate(v, W, H, synth.PATH_CAMERA, 0.01, tile, ox, oy, phase, 0.8)
+    rq, _, _, tiles, tq = nrc.paths_terminate(V, W, H, synth.PATH_CAMERA, prm)
+    _, ref_tiles = _checked(v, rq, tiles, 0.01, tile, ox, oy, phase)
     w0 = synth.xavier_weights(DIMS, seed=22)
     tail = O.infer(w0, DIMS, tq.cpu().numpy())  # the cache's values at the tails (FP64 oracle)
     ref_rec, ref_tg = O.paths_records(v, ref_tiles, tail, 0.8)

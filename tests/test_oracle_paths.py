@@ -127,3 +127,34 @@ def test_composite_closed_form(O):
     assert np.allclose(T, np.prod(f[:, :5], axis=1), rtol=1e-12)
     rgb = np.random.default_rng(8).uniform(size=(200, 3))
     assert np.allclose(O.paths_composite(E, T, rgb), ref_E + np.prod(f[:, :5], axis=1) * rgb)
+
+
+def test_decision_checker_accepts_the_definitions_decisions(O):
+    v = synth.make_paths(40, 30, 8, seed=4)
+    n, _, _, tiles = O.paths_terminate(v, 40, 30, synth.PATH_CAMERA, 0.01, 4, 1, 2, 5, 0.8)
+    assert O.paths_check_decisions(v, 40, 30, synth.PATH_CAMERA, 0.01, 4, 1, 2, 5, 0.8, n, tiles) == (True, 0)
+    # a path end or a suffix end moved past a clear decision is rejected
+    p = int(np.argmax(n < 6))
+    n2 = n.copy()
+    n2[p] += 1
+    assert not O.paths_check_decisions(v, 40, 30, synth.PATH_CAMERA, 0.01, 4, 1, 2, 5, 0.8, n2, tiles)[0]
+    t2 = np.array(tiles)
+    k = int(np.argmax((t2[:, 0] >= 0) & (t2[:, 3] == 0) & (t2[:, 2] < 7)))
+    t2[k, 2] += 1
+    assert not O.paths_check_decisions(v, 40, 30, synth.PATH_CAMERA, 0.01, 4, 1, 2, 5, 0.8, n, t2)[0]
+
+
+def test_decision_checker_accepts_either_side_of_the_threshold(O):
+    # c chosen so that c a_0 sits 1e-7 (relative) below a(x_1): FP64 ends the path at x_1; FP32 may
+    # take that decision the other way and end it at x_2 (the next decision is clear); x_3 is wrong
+    v = _line_path([0.01, 0.5, 0.5])
+    s1 = float(v[0, 1, 2]) - float(v[0, 0, 2])
+    c = s1 * s1 * (4.0 * math.pi) * (1.0 - 1e-7)
+    n, _, _, tiles = O.paths_terminate(v, 1, 1, (0, 0, 0), c, 1, 0, 0, -1, 0.8)
+    assert n[0] == 1
+    assert 1e-7 < O.termination_band(4)
+    s, thr = O._termination_terms(v, (0, 0, 0), c)
+    for end, ok in ((1, True), (2, True), (3, False)):
+        t = [(0, end, O._suffix_end(s[0], thr[0], end, 4), 0)]
+        got = O.paths_check_decisions(v, 1, 1, (0, 0, 0), c, 1, 0, 0, -1, 0.8, np.array([end]), t)
+        assert got == (ok, 1 if ok and end != 1 else got[1]), (end, got)
