@@ -2,6 +2,7 @@
 
     python -m paper_2106_12372_gb300.profile_case --what infer --n 2073600 --dtype fp16 --iters 3
     python -m paper_2106_12372_gb300.profile_case --what train --batch 16384 --dtype fp16 --iters 3
+    python -m paper_2106_12372_gb300.profile_case --what frame --n 2073600 --steps 4 --iters 3
     python -m paper_2106_12372_gb300.profile_case --what paths --width 1920 --height 1080 --iters 3
 
 ``paths`` runs the training-record pipeline around the query (terminate, the
@@ -40,9 +41,11 @@ def main() -> None:
     rec = torch.from_numpy(synth.make_records(args.n, seed=6)).to(dev) if args.what != "train" else None
     rgb = torch.empty((args.n, 3), device=dev) if rec is not None else None
     for it in range(args.iters):
-        if args.what in ("infer", "frame"):
+        if args.what == "frame":  # the fused frame: one launch of queries and training steps
+            cache.frame(rec, rgb, pool, tgt, args.batch, args.steps, synth.frame_seed(5, it))
+        if args.what == "infer":
             cache.infer(rec, rgb)
-        if args.what in ("train", "frame"):
+        if args.what == "train":
             for s in range(args.steps):
                 cache.train_step(pool, tgt, args.batch, synth.frame_seed(5, it), s)
     torch.cuda.synchronize()
