@@ -707,7 +707,8 @@ __global__ void __launch_bounds__(kFrameThreads, 1) k_frame_tc(const __grid_cons
     };
     // tickets: the first two tiles at once, then one per tile, published in
     // the tile's output layer so that the atomic's latency is hidden
-    if (rit == 0) s_next[slot] = int(atomicAdd(&p.sync[1], 2u));
+    const int lead_t = 32 * (slot & 3);  // lane 0 of the slot's lead warp (as in tile_layers)
+    if (rit == lead_t) s_next[slot] = int(atomicAdd(&p.sync[1], 2u));
     named_sync(1 + slot, 128);
     int64_t cur = s_next[slot];
     int64_t nxt = cur + 1;
@@ -733,7 +734,7 @@ __global__ void __launch_bounds__(kFrameThreads, 1) k_frame_tc(const __grid_cons
       const int64_t row = cur * kTile + rit;
       prefetch(nxt, buf ^ 1);
       int nxt2 = 0;
-      if (rit == 0) nxt2 = int(atomicAdd(&p.sync[1], 1u));
+      if (rit == lead_t) nxt2 = int(atomicAdd(&p.sync[1], 1u));
       cp_async_wait<1>();
       float r[kRecFloats];
       rs.read(buf, r);
@@ -742,7 +743,7 @@ __global__ void __launch_bounds__(kFrameThreads, 1) k_frame_tc(const __grid_cons
       encode_to_tmem<MODE, BF16>(r, p.pad, st.t_act);
       tile_layers<BF16>(p.img, p.net.n_mats, st, sw_base, slot, rit, &bar_q[slot], phase, p.err,
                         row < p.n_q ? p.rgb + row * 3 : nullptr, fac_row, rs.rot, [&]() {
-                          if (rit == 0) s_next[slot] = nxt2;
+                          if (rit == lead_t) s_next[slot] = nxt2;
                         });
       cur = nxt;
       nxt = s_next[slot];

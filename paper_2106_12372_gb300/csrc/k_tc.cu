@@ -360,8 +360,9 @@ __global__ void __launch_bounds__(kInferThreads, 1) k_infer_fp8(const __grid_con
     for (int l = 0; l < p.n_mats; ++l) {
       fence_before();
       named_sync(1 + slot, 128);
-      if (rit < 32) {
-        // the slot's first warp forms the (warp-uniform) descriptor; one elected thread issues
+      if ((rit >> 5) == (slot & 3)) {
+        // the slot's lead warp (warp slot % 4, as in tile_layers) forms the
+        // (warp-uniform) descriptor; one elected thread issues
         fence_after();
         const uint32_t idesc = idesc_e4m3(128, p.img.rows[l]);
         const uint64_t bd = sdesc_sw64(sw_base + uint32_t(img8_offset_of(p.img, l)), 512);
@@ -374,7 +375,7 @@ __global__ void __launch_bounds__(kInferThreads, 1) k_infer_fp8(const __grid_con
         }
         __syncwarp();
       }
-      if (rit == 0) mbar_wait(&bar_mma[slot], phase, p.err);
+      if (rit == 32 * (slot & 3)) mbar_wait(&bar_mma[slot], phase, p.err);
       named_sync(1 + slot, 128);
       phase ^= 1u;
       fence_after();

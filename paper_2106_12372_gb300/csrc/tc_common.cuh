@@ -67,9 +67,13 @@ template <bool BF16, class Hook = NoHook>
 __device__ __forceinline__ void tile_layers(const ImageShape& img, int n_mats, const SlotTmem& st, uint32_t sw_base,
                                             int slot, int rit, uint64_t* bar, uint32_t& phase, int* err, float* out,
                                             const uint8_t* fac_row, uint32_t rot, Hook last_layer = Hook()) {
-  // the slot's first warp computes the (warp-uniform) descriptors together;
-  // one elected thread issues, thread 0 waits
-  const bool w0 = rit < 32;
+  // the slot's lead warp computes the (warp-uniform) descriptors together;
+  // one elected thread issues, the warp's lane 0 waits.  The lead is warp
+  // slot % 4 of the warpgroup: warp w runs on SM sub-partition w % 4, so the
+  // slots' issue and wait work is spread over the four schedulers instead of
+  // slowing one of them (and with it every slot's epilogue there).
+  const int lead = slot & 3;
+  const bool w0 = (rit >> 5) == lead;
   for (int l = 0; l < n_mats; ++l) {
     if (l + 1 == n_mats) last_layer();
     uint32_t idesc = 0;
@@ -91,7 +95,7 @@ __device__ __forceinline__ void tile_layers(const ImageShape& img, int n_mats, c
       }
       __syncwarp();
       // one thread waits for the MMAs; the rest of the warpgroup sleeps at the barrier
-      if (rit == 0) mbar_wait(bar, phase, err);
+      if (rit == 32 * lead) mbar_wait(bar, phase, err);
     }
     named_sync(1 + slot, 128);
     phase ^= 1u;
