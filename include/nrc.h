@@ -65,7 +65,8 @@ typedef enum nrc_status {
   NRC_ERR_OOM = 3,
   NRC_ERR_TIMEOUT = 4,
   NRC_ERR_UNSUPPORTED = 5,
-  NRC_ERR_BUSY = 6 /* not admitted now (memory budget or frame slot in use): retry later */
+  NRC_ERR_BUSY = 6, /* not admitted now (memory budget or frame slot in use): retry later */
+  NRC_ERR_BOUNDS = 7 /* a device bounds check failed; raised only by a library built with NRC_DEBUG */
 } nrc_status;
 
 /* Arithmetic type of the MLP's matrix products.  NRC_FP32: FP32 SIMT FMA
@@ -237,7 +238,10 @@ NRC_API nrc_status nrc_set_state(nrc_cache* cache, const float* weights, const f
 NRC_API nrc_status nrc_set_path(nrc_cache* cache, int32_t path);
 
 /* Synchronises `stream`, then reads and clears the device error word:
- * NRC_ERR_TIMEOUT if a bounded device wait gave up since the last check. */
+ * NRC_ERR_TIMEOUT if a bounded device wait gave up since the last check;
+ * NRC_ERR_BOUNDS if a device bounds check of an NRC_DEBUG build failed (the
+ * access it guarded was skipped; the results of the calls since the last
+ * check are then undefined). */
 NRC_API nrc_status nrc_check_error(nrc_cache* cache, nrc_stream stream);
 
 /* Number of kernels the library launched on this cache since creation. */

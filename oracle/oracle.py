@@ -21,7 +21,11 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "nrc_oracle.cpp")
-_LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
+# NRC_ORACLE_SANITIZE=1: the oracle built with AddressSanitizer and
+# UndefinedBehaviorSanitizer (load it with libasan preloaded)
+_SANITIZE = os.environ.get("NRC_ORACLE_SANITIZE", "") == "1"
+_SAN_FLAGS = ["-fsanitize=address,undefined", "-fno-sanitize-recover=undefined", "-fno-omit-frame-pointer", "-g"]
+_LIB_PATH = os.path.join(_HERE, "_build", "liboracle_san.so" if _SANITIZE else "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
@@ -35,7 +39,7 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         subprocess.check_call(["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-pthread",
-                               _SRC, "-o", tmp])
+                               _SRC, "-o", tmp] + (_SAN_FLAGS if _SANITIZE else []))
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 

@@ -2,6 +2,14 @@
 
 Each translation unit is compiled in parallel, then linked into one shared
 library with a C ABI (``include/nrc.h``).  No PyTorch headers are involved.
+
+Variants (``build(variant=...)``, ``python build.py --variant V``), each its
+own library ``libnrc_V.so`` and object folder:
+  san    the host code compiled and linked with AddressSanitizer and
+         UndefinedBehaviorSanitizer (load it with libasan preloaded);
+  debug  ``-DNRC_DEBUG``: device-side bounds checks that set the error word
+         (NRC_ERR_BOUNDS through nrc_check_error) instead of accessing out of
+         range.
 """
 from __future__ import annotations
 
@@ -15,6 +23,17 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnrc.so")
+VARIANTS = {
+    "": [],
+    # (one sanitizer per -Xcompiler: nvcc splits its values at commas)
+    "san": ["-Xcompiler", "-fsanitize=address", "-Xcompiler", "-fsanitize=undefined", "-Xcompiler",
+            "-fno-omit-frame-pointer", "-Xcompiler", "-fno-sanitize-recover=undefined"],
+    "debug": ["-DNRC_DEBUG"],
+}
+
+
+def lib_path(variant: str = "") -> str:
+    return LIB if not variant else os.path.join(HERE, f"libnrc_{variant}.so")
 SOURCES = ["nrc_api.cu", "k_simt.cu", "k_tc.cu", "k_plain.cu", "nrc_noalloc.cu", "nrc_batch.cu", "nrc_serve.cu", "k_shampoo.cu", "k_paths.cu", "k_frame.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -39,16 +58,24 @@ def _deps_mtime() -> float:
     return max(os.path.getmtime(p) for p in paths)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile (if stale) and return the path of libnrc.so."""
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, variant: str | None = None) -> str:
+    """Compile (if stale) and return the path of libnrc.so (or of a variant;
+    by default the one NRC_LIB_VARIANT names)."""
+    if variant is None:
+        variant = os.environ.get("NRC_LIB_VARIANT", "")
+    if variant not in VARIANTS:
+        raise ValueError(f"unknown build variant {variant!r}")
+    lib = lib_path(variant)
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _deps_mtime():
+        return lib
+    obj_dir = BUILD if not variant else BUILD + "_" + variant
+    os.makedirs(obj_dir, exist_ok=True)
     cc = nvcc()
+    extra = VARIANTS[variant]
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [cc, "-c", os.path.join(CSRC, src), "-o", obj] + flags(verbose)
+        obj = os.path.join(obj_dir, src.replace(".cu", ".o"))
+        cmd = [cc, "-c", os.path.join(CSRC, src), "-o", obj] + flags(verbose) + extra
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{res.stdout}\n{res.stderr}")
@@ -58,14 +85,15 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + f".tmp{os.getpid()}"
-    res = subprocess.run([cc, "-shared", "-o", tmp] + objs + ARCH + ["-Xcompiler", "-fPIC", "-lpthread"], capture_output=True,
-                         text=True)
+    tmp = lib + f".tmp{os.getpid()}"
+    res = subprocess.run([cc, "-shared", "-o", tmp] + objs + ARCH + ["-Xcompiler", "-fPIC", "-lpthread"] + extra,
+                         capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    v = sys.argv[sys.argv.index("--variant") + 1] if "--variant" in sys.argv else None
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, variant=v))

@@ -180,7 +180,8 @@ __device__ __forceinline__ void frame_train(const FrameParams& p, uint8_t* sw, u
           float rec[kRecFloats], tg[3] = {0.f, 0.f, 0.f}, fac[3] = {1.f, 1.f, 1.f};
           if (row < p.batch) {
             const uint64_t idx = uint64_t(s) * uint64_t(p.batch) + uint64_t(row);
-            const int64_t src = int64_t((p.a * idx + p.c) % uint64_t(p.n_pool));
+            int64_t src = int64_t((p.a * idx + p.c) % uint64_t(p.n_pool));
+            if (!NRC_DCHECK(src >= 0 && src < p.n_pool, p.err)) src = 0;
             load_record(p.pool, src, rec);
             tg[0] = __ldg(p.target + src * 3);
             tg[1] = __ldg(p.target + src * 3 + 1);
@@ -354,6 +355,7 @@ __device__ __forceinline__ void frame_train(const FrameParams& p, uint8_t* sw, u
     if (o < R) {
 #pragma unroll
       for (int c = 0; c < 4; ++c)
+        if (NRC_DCHECK(p.net.w_off[l] + ((4 * q + c) * R + o) * 4 + 3 < p.net.n_params, p.err))
         *reinterpret_cast<float4*>(P + p.net.w_off[l] + ((4 * q + c) * R + o) * 4) =
             make_float4(__uint_as_float(v[4 * c]), __uint_as_float(v[4 * c + 1]), __uint_as_float(v[4 * c + 2]),
                         __uint_as_float(v[4 * c + 3]));
@@ -541,8 +543,9 @@ __device__ __forceinline__ void frame_train(const FrameParams& p, uint8_t* sw, u
         float4 t4[kSumBatch];
 #pragma unroll
         for (int u = 0; u < kSumBatch; ++u)
-          t4[u] = (k0 + u < k_hi) ? __ldcg(reinterpret_cast<const float4*>(src + size_t(k0 + u) * stride))
-                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+          t4[u] = (k0 + u < k_hi && NRC_DCHECK(size_t(q_lo + qd) * 4 + 3 < stride, p.err))
+                      ? __ldcg(reinterpret_cast<const float4*>(src + size_t(k0 + u) * stride))
+                      : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
         for (int u = 0; u < kSumBatch; ++u) {
           acc.x += t4[u].x;
@@ -564,7 +567,8 @@ __device__ __forceinline__ void frame_train(const FrameParams& p, uint8_t* sw, u
       p.m[pi] = m1;
       p.v[pi] = v1;
       const int qq = pi - p.net.w_off[li];
-      const uint32_t off = uint32_t(p.img.off[li]) + sw128_offset(uint32_t(qq / 64), uint32_t(qq % 64));
+      uint32_t off = uint32_t(p.img.off[li]) + sw128_offset(uint32_t(qq / 64), uint32_t(qq % 64));
+      if (!NRC_DCHECK(off + 2 <= uint32_t(p.img_bytes), p.err)) off = 0;
       if (BF16)
         *reinterpret_cast<__nv_bfloat16*>(p.img_work + off) = __float2bfloat16_rn(w1);
       else

@@ -684,7 +684,8 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(const __grid_cons
     float4* Pl = reinterpret_cast<float4*>(P + p.w_off[l]);
     for (int e = tid; e < dout * 16; e += kTrainThreads) {
       const int o = e >> 4, c = e & 15;  // 16-byte chunk c of row o: inputs 4c .. 4c+3
-      Pl[e] = *reinterpret_cast<const float4*>(S + o * 64 + (c & 8) * 4 + (((c & 7) ^ (o & 7)) << 2));
+      if (NRC_DCHECK(p.w_off[l] + 4 * e + 3 < p.n_params, p.err))
+        Pl[e] = *reinterpret_cast<const float4*>(S + o * 64 + (c & 8) * 4 + (((c & 7) ^ (o & 7)) << 2));
     }
   };
 
@@ -694,7 +695,8 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(const __grid_cons
     float rec[kRecFloats], tg[3] = {0.f, 0.f, 0.f}, fac[3] = {1.f, 1.f, 1.f};
     if (valid) {
       const uint64_t i = uint64_t(J.step) * uint64_t(J.batch) + uint64_t(j);
-      const int64_t src = int64_t((J.a * i + J.c) % uint64_t(J.n_pool));
+      int64_t src = int64_t((J.a * i + J.c) % uint64_t(J.n_pool));
+      if (!NRC_DCHECK(src >= 0 && src < J.n_pool, p.err)) src = 0;
       load_record(J.pool, src, rec);
       if (p.factor) {
 #pragma unroll

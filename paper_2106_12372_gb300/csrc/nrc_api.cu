@@ -704,6 +704,7 @@ nrc_status nrc_check_error(nrc_cache* c, nrc_stream stream) {
   // a frame launch that gave up may have left its counters part-way
   if (h != 0 && c->frame_sync) e = cudaMemset(c->frame_sync, 0, 64);
   if (e != cudaSuccess) return cuda_status(e, "nrc_check_error");
+  if (h & kErrBounds) return set_error("a device bounds check failed (NRC_DEBUG build; the access was skipped)"), NRC_ERR_BOUNDS;
   if (h & kErrTimeout) return set_error("a bounded device wait timed out"), NRC_ERR_TIMEOUT;
   return NRC_OK;
 }

@@ -22,6 +22,17 @@ constexpr int kMaxBatch = 1 << 16;  // training records per step
 
 // Device error word bits.
 constexpr int kErrTimeout = 1;
+constexpr int kErrBounds = 2;  // a device bounds check of an NRC_DEBUG build failed
+
+// NRC_DCHECK(cond, err): in a build with NRC_DEBUG defined, evaluates cond
+// and, where it is false, sets kErrBounds in the error word *err and yields
+// false, so that the caller skips the access it guards; otherwise it is the
+// constant true and the guarded access always runs.
+#ifdef NRC_DEBUG
+#define NRC_DCHECK(cond, err) ((cond) ? true : (atomicOr((err), ::nrc::kErrBounds), false))
+#else
+#define NRC_DCHECK(cond, err) true
+#endif
 // Bounded device waits give up after this many nanoseconds.
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;
 

@@ -15,10 +15,13 @@ import threading
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libnrc.so")
+# NRC_LIB_VARIANT=san|debug selects a variant build (build.py) instead of libnrc.so
+VARIANT = os.environ.get("NRC_LIB_VARIANT", "")
+LIB_PATH = os.path.join(HERE, f"libnrc_{VARIANT}.so" if VARIANT else "libnrc.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "nrc.h")
 
-NRC_OK, NRC_ERR_INVALID_ARG, NRC_ERR_CUDA, NRC_ERR_OOM, NRC_ERR_TIMEOUT, NRC_ERR_UNSUPPORTED, NRC_ERR_BUSY = range(7)
+NRC_OK, NRC_ERR_INVALID_ARG, NRC_ERR_CUDA, NRC_ERR_OOM, NRC_ERR_TIMEOUT, NRC_ERR_UNSUPPORTED, NRC_ERR_BUSY, \
+    NRC_ERR_BOUNDS = range(8)
 FP32, FP16, BF16, FP8 = 0, 1, 2, 3
 ENC_CHEAP, ENC_EXACT = 0, 1
 LOSS_LUMINANCE, LOSS_PER_CHANNEL = 0, 1
