@@ -275,32 +275,49 @@ def run_batched(queries, dtype: str, frames: int, flush):
     losses = [torch.zeros(1, device=dev) for _ in range(16)]
     s = torch.cuda.Stream()
     b = nrc.Batch(caches)
+    bl = [int(x) for x in bt]
+    sd = torch.zeros(16, dtype=torch.int64, device=dev)  # this frame's seeds, read by the gradient kernel
+
+    def seeds(f):
+        v = [synth.frame_seed(2106 + 100 * k, f) for k in range(16)]
+        return torch.tensor([x - (1 << 64) if x >= 1 << 63 else x for x in v], dtype=torch.int64)
+
     with torch.cuda.stream(s):
         unit = b.autotune(recs, rgbs, stream=s)
         b.infer(recs, rgbs, stream=s)
+        sd.copy_(seeds(0))
+        b.train_step_dev(pools, tgts, bl, sd, 0, losses, stream=s)  # uploads the step's descriptors
         s.synchronize()
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g, stream=s):
+        # the whole frame -- query launch, gradient launch, Adam launch -- in one graph; and the query
+        # launch alone in another, to split the frame's time between queries and training
+        gq = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gq, stream=s):
             b.infer(recs, rgbs, stream=s)
-        bl = [int(x) for x in bt]
+        gf = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gf, stream=s):
+            b.infer(recs, rgbs, stream=s)
+            b.train_step_dev(pools, tgts, bl, sd, 0, losses, stream=s)
 
         def frame(f, ev=None):
+            sd.copy_(seeds(f))  # 128 bytes host -> device, outside the events
             if ev:
                 ev[0].record(s)
-            g.replay()
+            gf.replay()
             if ev:
                 ev[1].record(s)
-            b.train_step(pools, tgts, bl, [synth.frame_seed(2106 + 100 * k, f) for k in range(16)], 0, losses,
-                         stream=s)
-            if ev:
-                ev[2].record(s)
 
         for f in range(3):
-            frame(f)
-        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(frames)]
+            frame(1 + f)
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(frames)]
         for f in range(frames):
             flush.zero_()
-            frame(3 + f, evs[f])
+            frame(4 + f, evs[f])
+        qev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(frames)]
+        for f in range(frames):
+            flush.zero_()
+            qev[f][0].record(s)
+            gq.replay()
+            qev[f][1].record(s)
         # the same work as 16 separate caches, one query and one training call each
         sev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(5)]
         for f in range(5):
@@ -314,22 +331,27 @@ def run_batched(queries, dtype: str, frames: int, flush):
         s.synchronize()
     for c in caches:
         c.check_error()
-    ms = [e[0].elapsed_time(e[2]) for e in evs]
-    inf = [e[0].elapsed_time(e[1]) for e in evs]
+    ms = [e[0].elapsed_time(e[1]) for e in evs]
+    inf = [e[0].elapsed_time(e[1]) for e in qev]
     seq = [e[0].elapsed_time(e[1]) for e in sev[1:]]
     q = int(nq.sum())
-    flop = FLOP_QUERY * q + FLOP_RECORD * int(bt.sum())
-    med = statistics.median(ms)
+    qflop, tflop = FLOP_QUERY * q, FLOP_RECORD * int(bt.sum())
+    med, qmed = statistics.median(ms), statistics.median(inf)
     b.close()
     for c in caches:
         c.close()
     return {
         "workload": "16 caches: queries log-uniform [4096, 2097152], one training step of log-uniform [4096, 65536] "
-                    "records each; query launch replayed from a CUDA graph; L2 flushed between frames",
+                    "records each; the whole frame (query, gradient and Adam launches) replayed from one CUDA "
+                    "graph, this frame's seeds written to the device before each replay; L2 flushed between frames",
         "queries": q, "train_records": int(bt.sum()), "frames": frames,
-        "ms_median": med, "ms_p99": float(np.percentile(ms, 99)), "infer_ms_median": statistics.median(inf),
-        "mqueries_per_s": q / (med / 1e3) / 1e6, "tflops": flop / (med / 1e3) / 1e12,
-        "unit_tiles_autotuned": unit, "launches_per_frame": 3,
+        "ms_median": med, "ms_p99": float(np.percentile(ms, 99)), "infer_ms_median": qmed,
+        "train_ms_median": med - qmed,
+        "mqueries_per_s": q / (med / 1e3) / 1e6, "tflops": (qflop + tflop) / (med / 1e3) / 1e12,
+        "query_tflops": qflop / (qmed / 1e3) / 1e12,
+        "train_tflops": tflop / ((med - qmed) / 1e3) / 1e12 if med > qmed else None,
+        "split_note": "query time from the query launch alone (its own graph); training = frame - query",
+        "unit_tiles_autotuned": unit, "launches_per_frame": 3, "launches_in_graph": 3,
         "sequential_16_caches_ms_median": statistics.median(seq),
     }
 
@@ -554,9 +576,10 @@ def cpu_oracle_small(seed: int = 2107):
     return (time.perf_counter() - t0) * 1e3, int(os.environ.get("ORACLE_THREADS", os.cpu_count() or 1))
 
 
-def run_serving(queries, dtype: str, seconds: float):
+def run_serving(queries, dtype: str, seconds: float, rate_scale: float = 1.0):
     """Eight viewports (4 x 1920x1080, 4 x 3840x2160) with Poisson frame
-    arrivals at 30-120 Hz each (rates seeded), served by the continuous-
+    arrivals at 30-120 Hz each (rates seeded; all multiplied by rate_scale
+    for the load sweep), served by the continuous-
     batching server under a 16 GB memory budget; each frame is a cache query
     for every pixel plus 4 training steps of 16,384 records from the
     viewport's resident 65,536-record pool.  Latency runs from the frame's
@@ -580,7 +603,7 @@ def run_serving(queries, dtype: str, seconds: float):
             r, _, _ = srv.buffers(vid, slot)
             for j in range(n // N_QUERIES):
                 r[j * N_QUERIES:(j + 1) * N_QUERIES].copy_(queries[(j + slot) % 2])
-        vps.append((vid, n, float(rng.uniform(30.0, 120.0))))
+        vps.append((vid, n, float(rng.uniform(30.0, 120.0)) * rate_scale))
     torch.cuda.synchronize()
     info0 = srv.info()
     # warm-up: two frames per viewport
@@ -629,7 +652,7 @@ def run_serving(queries, dtype: str, seconds: float):
     return {
         "workload": "8 viewports (4 x 1920x1080, 4 x 3840x2160), Poisson arrivals 30-120 Hz each, per frame all "
                     "pixels queried + 4 x 16,384-record training steps; 16 GB admission budget",
-        "seconds": seconds, "frames": len(done), "failed": int(sum(d.failed for d in done)),
+        "seconds": seconds, "rate_scale": rate_scale, "frames": len(done), "failed": int(sum(d.failed for d in done)),
         "p50_frame_ms": float(np.percentile(lat, 50)), "p99_frame_ms": float(np.percentile(lat, 99)),
         "max_frame_ms": float(lat.max()), "mean_batch_frames": float(np.mean([d.batch_frames for d in done])),
         "aggregate_mqueries_per_s": q / span / 1e6, "offered_mqueries_per_s": offered / 1e6,
@@ -747,10 +770,16 @@ def run_gpu(args):
             plain_ms.append(pev[0].elapsed_time(pev[1]))
     plain.close()
 
-    batched = serving = shampoo = precision = paths = small = None
+    batched = serving = serving_sweep = shampoo = precision = paths = small = None
     if not args.no_extras and ws == 1 and args.dtype != "fp32":
         batched = run_batched(queries, args.dtype, 30, flush)
         serving = run_serving(queries, args.dtype, args.serve_seconds)
+        # the same viewports at 1x .. 8x their frame rates: toward saturation, where continuous batching
+        # merges frames (mean_batch_frames > 1)
+        keys = ("rate_scale", "offered_mqueries_per_s", "aggregate_mqueries_per_s", "p50_frame_ms", "p99_frame_ms",
+                "max_frame_ms", "mean_batch_frames", "frames", "failed")
+        serving_sweep = [{k: r[k] for k in keys} for r in
+                         (run_serving(queries, args.dtype, args.sweep_seconds, sc) for sc in (1.0, 2.0, 4.0, 8.0))]
         shampoo = run_shampoo(pool, tgt, args.dtype, 30, flush)
         precision = run_precision(queries, flush)
         paths = run_paths(args.dtype, flush)
@@ -803,6 +832,7 @@ def run_gpu(args):
         "plain_fp32_ms_per_frame": statistics.median(plain_ms) if plain_ms else None,
         "batched_caches": batched,
         "serving": serving,
+        "serving_sweep": serving_sweep,
         "shampoo": shampoo,
         "precision": precision,
         "paths": paths,
@@ -833,6 +863,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched-caches and serving measurements")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--sweep-seconds", type=float, default=2.0, help="arrivals per point of the serving load sweep")
     ap.add_argument("--ref-seconds", type=float, default=90.0, help="oracle work of the whole --impl reference run")
     args = ap.parse_args()
     if args.impl == "reference":

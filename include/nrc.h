@@ -285,6 +285,20 @@ NRC_API nrc_status nrc_batch_train_step(nrc_batch* batch, const float* const* po
                                         const uint64_t* frame_seed, int32_t step, float* const* loss_out,
                                         nrc_stream stream);
 
+/* nrc_batch_train_step with the frame seeds in DEVICE memory: frame_seed_dev
+ * is a device array of n_caches uint64 (8-byte aligned), read by the gradient
+ * kernel when it runs, which derives each cache's shuffle from it.  The step's
+ * descriptors then do not depend on the seeds; they are uploaded only when
+ * they differ from the previous upload (pools, batches, step, loss pointers),
+ * so repeated calls launch the two kernels only and can be captured in a CUDA
+ * graph together with nrc_batch_infer.  Replays train on whatever seeds the
+ * array holds then (write it, stream-ordered, before each replay).  Same
+ * results as nrc_batch_train_step with those seeds. */
+NRC_API nrc_status nrc_batch_train_step_dev(nrc_batch* batch, const float* const* pool, const float* const* target,
+                                            const int64_t* n_pool, const int64_t* batch_size,
+                                            const uint64_t* frame_seed_dev, int32_t step, float* const* loss_out,
+                                            nrc_stream stream);
+
 /* Sets the work-unit size of nrc_batch_infer (1 .. 4096 tiles; default 20). */
 NRC_API nrc_status nrc_batch_set_unit_tiles(nrc_batch* batch, int32_t unit_tiles);
 

@@ -28,6 +28,9 @@ struct Batch {
   // host: last uploaded query descriptors, pinned staging ring
   std::vector<BatchCache> h_caches;
   std::vector<BatchUnit> h_units;
+  // host: last uploaded training descriptors (zero-padded, compared bytewise)
+  std::vector<TrainJob> h_jobs;
+  std::vector<AdamJob> h_adam;
   uint8_t* pinned = nullptr;
   size_t slot_bytes = 0;
   cudaEvent_t ev[kRing] = {};
@@ -52,9 +55,14 @@ nrc_status batch_infer(Batch* b, nrc_cache* const* caches, int nc, const float* 
 // One training step of every cache with batch[c] > 0: one gradient launch,
 // one Adam launch.  CTAs are shared out in proportion to the caches' tiles
 // (train_tiles == 0) or set per cache from its own batch (train_tiles > 0,
-// which makes each cache's result independent of the other caches).
+// which makes each cache's result independent of the other caches).  The
+// frame seeds come from the host array frame_seed, or, when seed_dev is not
+// null, from the device array seed_dev[c] (read by the gradient kernel).
+// The descriptors are uploaded only when they differ from the last upload,
+// so with device seeds repeated calls launch kernels only.
 nrc_status batch_train_step(Batch* b, nrc_cache* const* caches, int nc, const float* const* pool,
                             const float* const* target, const int64_t* n_pool, const int64_t* batch,
-                            const uint64_t* frame_seed, int32_t step, float* const* loss_out, cudaStream_t st);
+                            const uint64_t* frame_seed, int32_t step, float* const* loss_out, cudaStream_t st,
+                            const uint64_t* seed_dev = nullptr);
 
 }  // namespace nrc

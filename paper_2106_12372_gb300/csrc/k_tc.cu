@@ -615,6 +615,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(const __grid_cons
   TrainJob J;
   if (p.jobs) {
     J = p.jobs[blockIdx.x];
+    if (J.seed) lcg_shuffle(J.n_pool, *J.seed, &J.a, &J.c);  // the frame seed lives on the device
   } else {
     J.pool = p.pool;
     J.target = p.target;
@@ -622,6 +623,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_train_tc(const __grid_cons
     J.batch = p.batch;
     J.a = p.a;
     J.c = p.c;
+    J.seed = nullptr;
     J.step = p.step;
     J.tile_begin = int(blockIdx.x);
     J.tile_end = int((p.batch + kTile - 1) / kTile);

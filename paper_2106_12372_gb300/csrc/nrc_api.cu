@@ -83,22 +83,7 @@ static uint64_t splitmix64(uint64_t& state) {
 }
 
 void lcg_params(int64_t n_pool, uint64_t frame_seed, uint64_t* a_out, uint64_t* c_out) {
-  const uint64_t N = uint64_t(n_pool);
-  uint64_t st = frame_seed;
-  const uint64_t h = splitmix64(st);
-  const uint64_t h2 = splitmix64(st);
-  uint64_t a = N >= 4 ? 1 + 4 * (h % (N / 4)) : 1;
-  auto gcd = [](uint64_t x, uint64_t y) {
-    while (y) {
-      const uint64_t t = x % y;
-      x = y;
-      y = t;
-    }
-    return x;
-  };
-  while (N > 1 && gcd(a, N) != 1) a += 2;
-  *a_out = a;
-  *c_out = N ? h2 % N : 0;
+  lcg_shuffle(n_pool, frame_seed, a_out, c_out);
 }
 
 // Xavier-uniform initial weights from SplitMix64 (stream 2 of the seed):

@@ -160,9 +160,12 @@ nrc_status batch_infer(Batch* b, nrc_cache* const* caches, int nc, const float* 
 
 nrc_status batch_train_step(Batch* b, nrc_cache* const* caches, int nc, const float* const* pool,
                             const float* const* target, const int64_t* n_pool, const int64_t* batch,
-                            const uint64_t* frame_seed, int32_t step, float* const* loss_out, cudaStream_t st) {
-  if (!pool || !target || !n_pool || !batch || !frame_seed || step < 0)
+                            const uint64_t* frame_seed, int32_t step, float* const* loss_out, cudaStream_t st,
+                            const uint64_t* seed_dev) {
+  if (!pool || !target || !n_pool || !batch || (!frame_seed && !seed_dev) || step < 0)
     return set_error("batched training: NULL argument or negative step"), NRC_ERR_INVALID_ARG;
+  if (seed_dev && (reinterpret_cast<uintptr_t>(seed_dev) & 7u))
+    return set_error("batched training: frame seeds must be 8-byte aligned"), NRC_ERR_INVALID_ARG;
   if (nc > b->max_caches) return set_error("batched training: %d caches, capacity %d", nc, b->max_caches), NRC_ERR_INVALID_ARG;
   std::vector<int64_t> tiles(size_t(nc), 0);
   int64_t total = 0;
@@ -201,25 +204,27 @@ nrc_status batch_train_step(Batch* b, nrc_cache* const* caches, int nc, const fl
       --used;
     }
   }
-  int slot;
-  uint8_t* h = ring_slot(b, &slot);
-  TrainJob* hj = reinterpret_cast<TrainJob*>(h);
-  AdamJob* ha = reinterpret_cast<AdamJob*>(h + up256(sizeof(TrainJob) * b->max_jobs));
+  // descriptors in zero-initialised vectors (padding included), so that an
+  // unchanged call compares equal to the last upload byte for byte
+  std::vector<TrainJob> hj(static_cast<size_t>(used));
+  std::vector<AdamJob> ha;
+  ha.reserve(size_t(nc));
   int j = 0, n_adam = 0;
   for (int c = 0; c < nc; ++c) {
     if (!tiles[c]) continue;
     nrc_cache* cc = caches[c];
-    uint64_t a, ic;
-    lcg_params(n_pool[c], frame_seed[c], &a, &ic);
+    uint64_t a = 0, ic = 0;
+    if (!seed_dev) lcg_params(n_pool[c], frame_seed[c], &a, &ic);
     const int j0 = j;
     for (int q = 0; q < k[c]; ++q, ++j) {
-      TrainJob& J = hj[j];
+      TrainJob& J = hj[size_t(j)];
       J.pool = pool[c];
       J.target = target[c];
       J.n_pool = n_pool[c];
       J.batch = batch[c];
       J.a = a;
       J.c = ic;
+      J.seed = seed_dev ? seed_dev + c : nullptr;
       J.step = step;
       J.tile_begin = int(tiles[c] * q / k[c]);
       J.tile_end = int(tiles[c] * (q + 1) / k[c]);
@@ -230,13 +235,39 @@ nrc_status batch_train_step(Batch* b, nrc_cache* const* caches, int nc, const fl
       J.bump_t = q == 0;
       J.inv3n = float(1.0 / (3.0 * double(batch[c])));
     }
-    ha[n_adam++] = AdamJob{cc->w, cc->m, cc->v, cc->cfg.ema ? cc->ema : nullptr, cc->wimg_ema, cc->t,
-                           b->d_partials + size_t(j0) * b->stride, k[c], cc->wimg,
-                           float(1.0 / (3.0 * double(batch[c]))), loss_out ? loss_out[c] : nullptr};
+    ha.emplace_back();  // value-initialised: padding zero
+    AdamJob& A = ha.back();
+    A.w = cc->w;
+    A.m = cc->m;
+    A.v = cc->v;
+    A.ema = cc->cfg.ema ? cc->ema : nullptr;
+    A.wimg_ema = cc->wimg_ema;
+    A.t_ctr = cc->t;
+    A.partials = b->d_partials + size_t(j0) * b->stride;
+    A.n_partials = k[c];
+    A.wimg = cc->wimg;
+    A.grad_scale = float(1.0 / (3.0 * double(batch[c])));
+    A.loss_out = loss_out ? loss_out[c] : nullptr;
+    ++n_adam;
   }
-  cudaError_t e = cudaMemcpyAsync(b->d_jobs, hj, sizeof(TrainJob) * j, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_adam, ha, sizeof(AdamJob) * n_adam, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaEventRecord(b->ev[slot], st);
+  cudaError_t e = cudaSuccess;
+  const bool same = hj.size() == b->h_jobs.size() && ha.size() == b->h_adam.size() &&
+                    !std::memcmp(hj.data(), b->h_jobs.data(), sizeof(TrainJob) * hj.size()) &&
+                    !std::memcmp(ha.data(), b->h_adam.data(), sizeof(AdamJob) * ha.size());
+  if (!same) {
+    int slot;
+    uint8_t* h = ring_slot(b, &slot);
+    std::memcpy(h, hj.data(), sizeof(TrainJob) * hj.size());
+    std::memcpy(h + up256(sizeof(TrainJob) * b->max_jobs), ha.data(), sizeof(AdamJob) * ha.size());
+    e = cudaMemcpyAsync(b->d_jobs, h, sizeof(TrainJob) * j, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(b->d_adam, h + up256(sizeof(TrainJob) * b->max_jobs), sizeof(AdamJob) * n_adam,
+                          cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev[slot], st);
+    if (e != cudaSuccess) return cuda_status(e, "batched training");
+    b->h_jobs.swap(hj);
+    b->h_adam.swap(ha);
+  }
   if (e == cudaSuccess) e = launch_train_batched(caches[0], b->d_jobs, j, st);
   if (e == cudaSuccess) e = launch_adam_batched(caches[0], b->d_adam, n_adam, st);
   for (int c = 0; c < nc; ++c) caches[c]->launches += 2;
@@ -301,6 +332,15 @@ nrc_status nrc_batch_train_step(nrc_batch* b, const float* const* pool, const fl
   if (!b) return set_error("nrc_batch_train_step: batch is NULL"), NRC_ERR_INVALID_ARG;
   return batch_train_step(b, b->caches.data(), int(b->caches.size()), pool, target, n_pool, batch, frame_seed, step,
                           loss_out, reinterpret_cast<cudaStream_t>(stream));
+}
+
+nrc_status nrc_batch_train_step_dev(nrc_batch* b, const float* const* pool, const float* const* target,
+                                    const int64_t* n_pool, const int64_t* batch, const uint64_t* frame_seed_dev,
+                                    int32_t step, float* const* loss_out, nrc_stream stream) {
+  if (!b) return set_error("nrc_batch_train_step_dev: batch is NULL"), NRC_ERR_INVALID_ARG;
+  if (!frame_seed_dev) return set_error("nrc_batch_train_step_dev: frame_seed_dev is NULL"), NRC_ERR_INVALID_ARG;
+  return batch_train_step(b, b->caches.data(), int(b->caches.size()), pool, target, n_pool, batch, nullptr, step,
+                          loss_out, reinterpret_cast<cudaStream_t>(stream), frame_seed_dev);
 }
 
 nrc_status nrc_batch_autotune(nrc_batch* b, const float* const* records, const int64_t* n, float* const* rgb,

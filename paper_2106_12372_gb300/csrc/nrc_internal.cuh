@@ -154,6 +154,7 @@ struct TrainJob {
   int64_t n_pool;
   int64_t batch;
   uint64_t a, c;       // the batch's shuffle (Sec. 3.5)
+  const uint64_t* seed;  // device: the frame seed to derive a, c from in the kernel (null: a, c as given)
   int step;
   int tile_begin, tile_end, tile_step;
   const uint8_t* wimg;
@@ -191,6 +192,38 @@ void make_image_shape(const NetShape& s, ImageShape* img);
 
 // Shuffle parameters (Sec. 3.5): perm(i) = (a*i + c) mod n_pool.
 void lcg_params(int64_t n_pool, uint64_t frame_seed, uint64_t* a, uint64_t* c);
+
+// The frame's shuffle of a pool of n_pool records (Sec. 3.5): the full-period
+// LCG i -> (a i + c) mod n_pool whose multiplier and increment come from
+// SplitMix64 (Steele, Lea & Flood 2014) of frame_seed; a is 1 mod 4 and
+// coprime to n_pool, the Hull-Dobell conditions.  Host and device compute it
+// alike (lcg_params is this on the host).
+__host__ __device__ __forceinline__ uint64_t splitmix64_next(uint64_t& state) {
+  state += 0x9E3779B97F4A7C15ull;
+  uint64_t z = state;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__host__ __device__ __forceinline__ void lcg_shuffle(int64_t n_pool, uint64_t frame_seed, uint64_t* a_out,
+                                                     uint64_t* c_out) {
+  const uint64_t N = uint64_t(n_pool);
+  uint64_t st = frame_seed;
+  const uint64_t h = splitmix64_next(st);
+  const uint64_t h2 = splitmix64_next(st);
+  uint64_t a = N >= 4 ? 1 + 4 * (h % (N / 4)) : 1;
+  auto gcd = [](uint64_t x, uint64_t y) {
+    while (y) {
+      const uint64_t t = x % y;
+      x = y;
+      y = t;
+    }
+    return x;
+  };
+  while (N > 1 && gcd(a, N) != 1) a += 2;
+  *a_out = a;
+  *c_out = N ? h2 % N : 0;
+}
 
 // Kernel launchers (each returns the launch's cudaError_t).
 // Grows the weight-gradient partial buffer to at least `count` partials.

@@ -145,6 +145,7 @@ def lib() -> ctypes.CDLL:
             "nrc_batch_destroy": (i32, [P]),
             "nrc_batch_infer": (i32, [P, P, P, P, P]),
             "nrc_batch_train_step": (i32, [P, P, P, P, P, P, i32, P, P]),
+            "nrc_batch_train_step_dev": (i32, [P, P, P, P, P, P, i32, P, P]),
             "nrc_batch_set_unit_tiles": (i32, [P, i32]),
             "nrc_batch_autotune": (i32, [P, P, P, P, P, P]),
             "nrc_batch_set_train_tiles": (i32, [P, i32]),
@@ -382,6 +383,16 @@ class Batch:
         lo = _ptr_array(losses) if losses is not None else None
         _check(lib().nrc_batch_train_step(self._h, _ptr_array(pools), _ptr_array(targets), n_pool, bs, fs, step, lo,
                                           _stream(stream)))
+
+    def train_step_dev(self, pools, targets, batches, seeds_dev, step: int, losses=None, stream=None) -> None:
+        """train_step with the frame seeds in a device tensor (int64 bits, one per cache), read when the kernel
+        runs: the call is capturable in a CUDA graph with the query launch."""
+        k = len(pools)
+        n_pool = (ctypes.c_int64 * k)(*[p.shape[0] for p in pools])
+        bs = (ctypes.c_int64 * k)(*batches)
+        lo = _ptr_array(losses) if losses is not None else None
+        _check(lib().nrc_batch_train_step_dev(self._h, _ptr_array(pools), _ptr_array(targets), n_pool, bs,
+                                              _ptr(seeds_dev), step, lo, _stream(stream)))
 
     def set_unit_tiles(self, u: int) -> None:
         _check(lib().nrc_batch_set_unit_tiles(self._h, u))

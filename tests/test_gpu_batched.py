@@ -141,3 +141,67 @@ def test_batch_rejects_mixed_configurations():
     f32 = nrc.Cache(dtype="fp32")
     with pytest.raises(nrc.NrcError):
         nrc.Batch([f32])
+
+
+
+def _i64(seeds):
+    return torch.tensor([x - (1 << 64) if x >= 1 << 63 else x for x in seeds], dtype=torch.int64)
+
+
+def test_batch_train_step_dev_equals_host_seeds_and_replays_in_a_graph():
+    """Frame seeds in device memory: the same bits as host seeds, eagerly and
+    from one captured graph (query launch + gradient launch + Adam launch)
+    replayed with new seeds written before each replay -- one training step
+    per frame, as the batched-caches frame runs it."""
+    bl = [4096, 129, 20_000]
+    pools, tgts = [], []
+    for k, n in enumerate(bl):
+        p, t = synth.make_training_pool(2 * n, seed=900 + k)
+        pools.append(dev(p))
+        tgts.append(dev(t))
+    recs = [dev(synth.make_records(n, seed=950 + k)) for k, n in enumerate((1000, 129, 5000))]
+    seeds = [[synth.frame_seed(970 + k, f) for k in range(3)] for f in range(3)]
+
+    ref_c = [nrc.Cache(dtype="fp16", seed=980 + k) for k in range(3)]
+    ref_b = nrc.Batch(ref_c)
+    ref_out = []
+    for f in range(3):
+        out = [torch.empty((r.shape[0], 3), device=DEV) for r in recs]
+        ref_b.infer(recs, out)
+        ref_b.train_step(pools, tgts, bl, seeds[f], 0)
+        ref_out.append(out)
+    torch.cuda.synchronize()
+
+    got_c = [nrc.Cache(dtype="fp16", seed=980 + k) for k in range(3)]
+    got_b = nrc.Batch(got_c)
+    sd = torch.zeros(3, dtype=torch.int64, device=DEV)
+    out = [torch.empty((r.shape[0], 3), device=DEV) for r in recs]
+    got_out = []
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        sd.copy_(_i64(seeds[0]))
+        got_b.infer(recs, out, stream=s)
+        got_b.train_step_dev(pools, tgts, bl, sd, 0, stream=s)  # uploads the descriptors
+        got_out.append([o.clone() for o in out])
+        s.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            got_b.infer(recs, out, stream=s)
+            got_b.train_step_dev(pools, tgts, bl, sd, 0, stream=s)
+        for f in (1, 2):
+            sd.copy_(_i64(seeds[f]))
+            g.replay()
+            got_out.append([o.clone() for o in out])
+        s.synchronize()
+    for f in range(3):
+        for k in range(3):
+            assert torch.equal(got_out[f][k], ref_out[f][k]), (f, k)
+    for a, b in zip(ref_c, got_c):
+        a.check_error()
+        b.check_error()
+        for x, y in zip(a.get_state(), b.get_state()):
+            assert np.array_equal(np.asarray(x), np.asarray(y))
+    for c in ref_c + got_c:
+        c.close()
+    ref_b.close()
+    got_b.close()
