@@ -150,8 +150,8 @@ __device__ __forceinline__ void train_grid_barrier(unsigned* ctr, unsigned targe
 
 template <int MODE, bool BF16>
 __device__ __forceinline__ void frame_train(const FrameParams& p, uint8_t* sw, uint32_t tmem, uint64_t* bar_w,
-                                            uint64_t* bar_mma, uint64_t* bar_full, uint64_t* bar_free, float* red,
-                                            const float* s_corr) {
+                                            uint64_t* bar_mma, uint64_t* bar_dw, uint64_t* bar_full,
+                                            uint64_t* bar_free, float* red, const float* s_corr) {
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
   const int b = blockIdx.x;
@@ -262,6 +262,11 @@ __device__ __forceinline__ void frame_train(const FrameParams& p, uint8_t* sw, u
         __syncwarp();
       };
       bool first = true;
+      // the previous tile's dW_0, issued behind this tile's layer 1 (not with
+      // its dW_1 behind layer 0), so that the chain waits for half as many
+      // weight-gradient MMAs at each tile boundary
+      bool dw0_pending = false, prev_first = false;
+      int prev_par = 0;
       for (int64_t i = b; i < tiles; i += T, ++j) {
         const int par = j & 1;
         const bool last_tile = i + T >= tiles;
@@ -271,11 +276,17 @@ __device__ __forceinline__ void frame_train(const FrameParams& p, uint8_t* sw, u
           const uint64_t bb = wk + uint64_t(p.img.off[l] >> 4);
           named_sync(kBarOps, kFrameCompute + 32);
           fence_after();
-          if (elect_one()) {
+          const bool lead = elect_one();
+          if (lead) {
 #pragma unroll
             for (int k = 0; k < 4; ++k)
               mma_ts(tmem, tmem + kActCol + uint32_t(8 * k), bb + uint64_t(2 * k), idesc, k > 0 ? 1u : 0u);
             mma_commit(bar_mma);
+          }
+          if (l == 1 && dw0_pending) {
+            issue_dw(0, prev_par, prev_first, lead);
+            if (lead) mma_commit(&bar_free[prev_par]);  // the previous tile's buffers are free
+            dw0_pending = false;
           }
           __syncwarp();
         }
@@ -293,16 +304,28 @@ __device__ __forceinline__ void frame_train(const FrameParams& p, uint8_t* sw, u
           __syncwarp();
         }
         // stage 0: the next tile's layer 0 first (the chain goes on), then
-        // dW_1 (deferred) and dW_0; their completion frees this tile's H_0
-        // buffer (producer) and the shared copies the next tile overwrites
+        // dW_1 (deferred); dW_0 follows behind the next tile's layer 1.  The
+        // step's last tile issues both now: bar_dw first (the weight
+        // gradients issued so far are final: the compute writes dW_2, dW_3
+        // behind dW_1 and dW_0), then bar_mma.  bar_free[par], once dW_0 is
+        // done, frees this tile's H_0 buffer (producer) and the shared copies
+        // the next tile overwrites.
         named_sync(kBarOps, kFrameCompute + 32);
         if (!last_tile) issue_layer0(j + 1);
         fence_after();
         const bool lead = elect_one();
-        issue_dw(1, par, first, lead);
-        issue_dw(0, par, first, lead);
-        if (lead && last_tile) mma_commit(bar_mma);
-        if (lead) mma_commit(&bar_free[par]);
+        if (last_tile) {
+          if (lead) mma_commit(bar_dw);
+          issue_dw(1, par, first, lead);
+          issue_dw(0, par, first, lead);
+          if (lead) mma_commit(bar_mma);
+          if (lead) mma_commit(&bar_free[par]);
+        } else {
+          issue_dw(1, par, first, lead);
+          dw0_pending = true;
+          prev_par = par;
+          prev_first = first;
+        }
         __syncwarp();
         first = false;
       }
@@ -376,9 +399,23 @@ __device__ __forceinline__ void frame_train(const FrameParams& p, uint8_t* sw, u
       const bool first_of_step = i == b;
 
       // ------------------------------------------------------------ forward
+      // The previous tile's dW_1 went out behind this tile's layer 0 and its
+      // dW_0 behind layer 1: H_1's shared copy (dW_1's operand buffer) waits
+      // in registers until layer 1's MMAs are done, and from H_3 on (whose
+      // buffer holds dW_0's delta operand) the copies wait for bar_free.
       float y[3] = {0.f, 0.f, 0.f};
+      uint32_t pk_h1[8];
+      bool freed = first_of_step;
+      auto wait_free = [&]() {
+        if (!freed) {
+          if ((tid & 31) == 0) mbar_wait(&bar_free[(j - 1) & 1], uint32_t(((j - 1) >> 1) & 1), p.err);
+          __syncwarp();
+          freed = true;
+        }
+      };
       for (int l = 0; l < L; ++l) {
         wait_mma();
+        if (l == 1 && !first_of_step) store_q_sw128(Hb + hbuf(1, par) * 16384, r, 2 * q, pk_h1);
         if (l + 1 < L) {
           uint32_t v[16], pk[8];
           tmem_ld16(t_acc, v);
@@ -387,23 +424,27 @@ __device__ __forceinline__ void frame_train(const FrameParams& p, uint8_t* sw, u
           tmem_st8(t_act, pk);  // the next layer's A operand
           tmem_st_wait();
           release_tmem();
-          // the previous tile's last dW MMAs (issued behind this tile's layer
-          // 0) read the buffers this tile writes from here on
-          if (l == 0 && !first_of_step) {
-            if ((tid & 31) == 0) mbar_wait(&bar_free[(j - 1) & 1], uint32_t(((j - 1) >> 1) & 1), p.err);
-            __syncwarp();
-          }
           // the copy the weight gradients (and the backward masks) read, behind the next layer's MMAs
-          store_q_sw128(Hb + hbuf(l + 1, par) * 16384, r, 2 * q, pk);
+          if (l == 0 && !first_of_step) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) pk_h1[k] = pk[k];
+          } else {
+            if (l + 1 >= 3) wait_free();
+            store_q_sw128(Hb + hbuf(l + 1, par) * 16384, r, 2 * q, pk);
+          }
           fence_proxy_async_smem();
-        } else if (q == 0) {
-          uint32_t v[4];
-          tmem_ld4(t_acc, v);
-          y[0] = __uint_as_float(v[0]);
-          y[1] = __uint_as_float(v[1]);
-          y[2] = __uint_as_float(v[2]);
+        } else {
+          if (l == 1 && !first_of_step) fence_proxy_async_smem();  // two layers: H_1 went out above
+          if (q == 0) {
+            uint32_t v[4];
+            tmem_ld4(t_acc, v);
+            y[0] = __uint_as_float(v[0]);
+            y[1] = __uint_as_float(v[1]);
+            y[2] = __uint_as_float(v[2]);
+          }
         }
       }
+      wait_free();  // (shallow nets: the delta buffers the backward writes next may be dW_0's operands)
 
       // --------------------------------------------------------------- loss
       if (q == 0) {
@@ -458,13 +499,23 @@ __device__ __forceinline__ void frame_train(const FrameParams& p, uint8_t* sw, u
           release();
         }
       }
-      if (last_tile) wait_mma();  // the step's last dW MMAs
+      if (last_tile) {
+        // bar_dw: every weight gradient but dW_1 and dW_0 is final; dW_2 and
+        // dW_3 go out while those two run, then the step's last MMAs
+        if ((tid & 31) == 0) mbar_wait(bar_dw, uint32_t(s & 1), p.err);
+        __syncwarp();
+        fence_after();
+        for (int l = 2; l < L && l < 4; ++l)
+          if (lanes_lo == ((l & 1) == 0)) write_dw(l);
+        wait_mma();
+      }
     }
 
     // ------------------------------------------- the CTA's partial of step s
-    // dW_{L-1} .. dW_4 went out during the last tile's backward (stages l >= 2
-    // wrote dW_{l+2}); the rest, final now, split over the two lane halves
-    for (int l = 0; l < L && l < 4; ++l)
+    // dW_{L-1} .. dW_2 went out during the last tile's backward (stages l >= 2
+    // wrote dW_{l+2}, then dW_3 and dW_2 at bar_dw); dW_1 and dW_0, final
+    // now, one per lane half
+    for (int l = 0; l < L && l < 2; ++l)
       if (lanes_lo == ((l & 1) == 0)) write_dw(l);
     {
       float sl = loss_acc;
@@ -630,7 +681,7 @@ __device__ __forceinline__ void copy_images(const FrameParams& p) {
 template <int MODE, bool BF16>
 __global__ void __launch_bounds__(kFrameThreads, 1) k_frame_tc(const __grid_constant__ FrameParams p) {
   extern __shared__ uint8_t smem_raw[];
-  __shared__ uint64_t bar_w, bar_mma, bar_full[2], bar_free[2];
+  __shared__ uint64_t bar_w, bar_mma, bar_dw, bar_full[2], bar_free[2];
   __shared__ uint64_t bar_wq, bar_q[kSlots];
   __shared__ uint32_t tmem_base_sh;
   __shared__ int s_next[kSlots];
@@ -650,6 +701,7 @@ __global__ void __launch_bounds__(kFrameThreads, 1) k_frame_tc(const __grid_cons
   if (tid == 0) {
     mbar_init(&bar_w, 1);
     mbar_init(&bar_mma, 1);
+    mbar_init(&bar_dw, 1);
     mbar_init(&bar_full[0], kProducerThreads);
     mbar_init(&bar_full[1], kProducerThreads);
     mbar_init(&bar_free[0], 1);
@@ -678,7 +730,7 @@ __global__ void __launch_bounds__(kFrameThreads, 1) k_frame_tc(const __grid_cons
   fence_after();
   const uint32_t tmem = tmem_base_sh;
 
-  if (trainer) frame_train<MODE, BF16>(p, sw, tmem, &bar_w, &bar_mma, bar_full, bar_free, red, s_corr);
+  if (trainer) frame_train<MODE, BF16>(p, sw, tmem, &bar_w, &bar_mma, &bar_dw, bar_full, bar_free, red, s_corr);
 
   // ---------------------------------------------------------- query role
   const int64_t n_tiles = (p.n_q + kTile - 1) / kTile;
