@@ -437,9 +437,35 @@ def run_precision(queries, flush, frames: int = 30):
     c.check_error()
     ms = float(np.median([e[0].elapsed_time(e[1]) for e in ev]))
     out["fp32_width128_7hidden"] = {"infer_ms": ms, "tflops": FLOP_QUERY_W128 * N_QUERIES / (ms / 1e3) / 1e12}
+    w128 = c.get_state()[0]
+    ref128 = c.infer(sample).cpu().numpy().astype(np.float64)
     c.close()
-    out["workload"] = ("1080p query batch per dtype (FP32: SIMT parity path; width 128: plain per-layer FP32 "
-                       "path); error against the FP32 path on 2,000 queries")
+    # ... and its FP16 / BF16 queries on the tensor cores (k_tc128), against the plain FP32 path
+    burst = peaks()[0]
+    tau128 = np.sqrt(np.mean(ref128 ** 2))
+    for dt in ("fp16", "bf16"):
+        c = nrc.Cache(dtype=dt, width=128, hidden_layers=7, seed=2106)
+        c.set_state(w128)
+        got = c.infer(sample).cpu().numpy().astype(np.float64)
+        err = np.abs(got - ref128) / np.maximum(np.abs(ref128), tau128)
+        for k in range(3):
+            c.infer(queries[k % 2], rgb)
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(frames)]
+        for k, e in enumerate(ev):
+            flush.zero_()
+            e[0].record(st)
+            c.infer(queries[k % 2], rgb)
+            e[1].record(st)
+        torch.cuda.synchronize()
+        c.check_error()
+        ms = float(np.median([e[0].elapsed_time(e[1]) for e in ev]))
+        tf = FLOP_QUERY_W128 * N_QUERIES / (ms / 1e3) / 1e12
+        out[f"{dt}_width128_7hidden"] = {"infer_ms": ms, "tflops": tf, "frac_of_peak": tf / burst,
+                                         "err_median": float(np.median(err)), "err_max": float(err.max())}
+        c.close()
+    out["workload"] = ("1080p query batch per dtype (FP32: SIMT parity path; width 128: plain per-layer FP32 path "
+                       "and the tensor-core FP16 / BF16 kernel); error against the FP32 path of the same width on "
+                       "2,000 queries")
     return out
 
 

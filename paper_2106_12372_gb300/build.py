@@ -34,7 +34,7 @@ VARIANTS = {
 
 def lib_path(variant: str = "") -> str:
     return LIB if not variant else os.path.join(HERE, f"libnrc_{variant}.so")
-SOURCES = ["nrc_api.cu", "k_simt.cu", "k_tc.cu", "k_plain.cu", "nrc_noalloc.cu", "nrc_batch.cu", "nrc_serve.cu", "k_shampoo.cu", "k_paths.cu", "k_frame.cu"]
+SOURCES = ["nrc_api.cu", "k_simt.cu", "k_tc.cu", "k_plain.cu", "nrc_noalloc.cu", "nrc_batch.cu", "nrc_serve.cu", "k_shampoo.cu", "k_paths.cu", "k_frame.cu", "k_tc128.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -486,7 +486,7 @@ __device__ __forceinline__ void adam_block(float* __restrict__ w, float* __restr
     while (l + 1 < net.n_mats && p >= net.w_off[l + 1]) ++l;
     const int q = p - net.w_off[l];
     const int o = q / net.dims[l], i = q % net.dims[l];
-    const uint32_t off = img.off[l] + sw128_offset(o, i);
+    const uint32_t off = img_offset(img, l, uint32_t(o), uint32_t(i));
     if (IMG == 1) {
       *reinterpret_cast<__half*>(wimg + off) = __float2half_rn(wn);
       if (ema) *reinterpret_cast<__half*>(wimg_ema + off) = __float2half_rn(en);
@@ -590,7 +590,7 @@ __global__ void k_build_image(const float* __restrict__ w, const __grid_constant
   while (l + 1 < net.n_mats && p >= net.w_off[l + 1]) ++l;
   const int q = p - net.w_off[l];
   const int o = q / net.dims[l], i = q % net.dims[l];
-  uint8_t* dst = wimg + img.off[l] + sw128_offset(o, i);
+  uint8_t* dst = wimg + img_offset(img, l, uint32_t(o), uint32_t(i));
   if (IMG == 1)
     *reinterpret_cast<__half*>(dst) = __float2half_rn(w[p]);
   else

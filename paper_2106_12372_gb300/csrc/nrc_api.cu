@@ -119,9 +119,17 @@ nrc_status check_cfg(const nrc_config* cfg) {
   if (cfg->hidden_layers < 1 || cfg->hidden_layers > kMaxMats - 1)
     return set_error("hidden_layers must be in [1, %d]", kMaxMats - 1), NRC_ERR_INVALID_ARG;
   if (cfg->width != 64 && cfg->width != 128) return set_error("width %d unsupported (64 or 128)", cfg->width), NRC_ERR_UNSUPPORTED;
-  if (cfg->width != 64 && (cfg->dtype != NRC_FP32 || cfg->path != NRC_PATH_PLAIN || cfg->optimizer != NRC_OPT_ADAM))
-    return set_error("width 128 runs on the plain FP32 path with Adam only (dtype NRC_FP32, path NRC_PATH_PLAIN)"),
-           NRC_ERR_UNSUPPORTED;
+  if (cfg->width != 64) {
+    // width 128: FP32 on the plain path, or FP16/BF16 queries on the tensor cores (trained on the plain FP32
+    // kernels); Adam only, and at most 7 hidden layers on the tensor cores (the 16-bit weight image stays in
+    // shared memory)
+    const bool plain32 = cfg->dtype == NRC_FP32 && cfg->path == NRC_PATH_PLAIN;
+    const bool tc16 = (cfg->dtype == NRC_FP16 || cfg->dtype == NRC_BF16) && cfg->hidden_layers <= 7 && !cfg->ema;
+    if (cfg->optimizer != NRC_OPT_ADAM || !(plain32 || tc16))
+      return set_error("width 128: dtype NRC_FP32 on the plain path, or NRC_FP16 / NRC_BF16 with at most 7 hidden "
+                       "layers and no weight average; Adam only"),
+             NRC_ERR_UNSUPPORTED;
+  }
   if (cfg->dtype < NRC_FP32 || cfg->dtype > NRC_FP8) return set_error("unknown dtype %d", cfg->dtype), NRC_ERR_INVALID_ARG;
   if (cfg->enc_mode != NRC_ENC_CHEAP && cfg->enc_mode != NRC_ENC_EXACT)
     return set_error("unknown enc_mode %d", cfg->enc_mode), NRC_ERR_INVALID_ARG;
@@ -321,8 +329,8 @@ nrc_status nrc_destroy(nrc_cache* c) {
 nrc_status nrc_set_path(nrc_cache* c, int32_t path) {
   if (!c) return set_error("cache is NULL"), NRC_ERR_INVALID_ARG;
   if (path != NRC_PATH_FUSED && path != NRC_PATH_PLAIN) return set_error("unknown path %d", path), NRC_ERR_INVALID_ARG;
-  if (path == NRC_PATH_FUSED && c->cfg.width != 64)
-    return set_error("the fused kernels take width 64 only"), NRC_ERR_UNSUPPORTED;
+  if (path == NRC_PATH_FUSED && c->cfg.width != 64 && c->cfg.dtype != NRC_FP16 && c->cfg.dtype != NRC_BF16)
+    return set_error("the fused kernels take width 64, or width 128 in FP16 / BF16"), NRC_ERR_UNSUPPORTED;
   c->cfg.path = path;
   return NRC_OK;
 }
@@ -345,6 +353,9 @@ static nrc_status infer_impl(nrc_cache* c, const float* rec, int64_t n, float* r
   cudaError_t e;
   if (c->cfg.path == NRC_PATH_PLAIN) {
     e = plain_infer(c, rec, n, rgb, st);
+  } else if (c->cfg.width == 128) {
+    e = launch_infer_tc128(c, rec, n, rgb, st);
+    c->launches += 1;
   } else if (c->cfg.dtype == NRC_FP8) {
     e = cudaSuccess;
     if (c->wimg8_dirty) {
@@ -395,7 +406,8 @@ static nrc_status train_impl(nrc_cache* c, const float* pool, const float* targe
   uint64_t a, cc;
   lcg_params(n_pool, frame_seed, &a, &cc);
   cudaError_t e;
-  if (c->cfg.path == NRC_PATH_PLAIN) {
+  if (c->cfg.path == NRC_PATH_PLAIN || c->cfg.width != 64) {
+    // (width 128 trains on the plain FP32 kernels; their Adam writes the 16-bit image the queries read)
     e = plain_train(c, pool, target, n_pool, batch, a, cc, step, loss_out, st);
     return cuda_status(e, "nrc_train_step (plain)");
   }
@@ -593,7 +605,8 @@ nrc_status nrc_frame_host(nrc_cache* c, const float* queries, int64_t n_q, float
   float* dt = reinterpret_cast<float*>(base + bq + br + bp);
   float* dl = reinterpret_cast<float*>(base + bq + br + bp + bt);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  if (n_q > 0 && c->cfg.path == NRC_PATH_FUSED && (c->cfg.dtype == NRC_FP16 || c->cfg.dtype == NRC_BF16))
+  if (n_q > 0 && c->cfg.path == NRC_PATH_FUSED && c->cfg.width == 64 &&
+      (c->cfg.dtype == NRC_FP16 || c->cfg.dtype == NRC_BF16))
     return frame_host_pipelined(c, queries, n_q, rgb, pool, target, n_pool, batch, n_steps, frame_seed, loss_out, dq, dr,
                                 dp, dt, dl, st);
   cudaError_t e = cudaSuccess;

@@ -34,6 +34,8 @@ nrc_status batch_check(nrc_cache* const* caches, int n_caches) {
     if (!caches[c]) return set_error("batched caches: cache %d is NULL", c), NRC_ERR_INVALID_ARG;
     if (caches[c]->cfg.dtype != NRC_FP16 && caches[c]->cfg.dtype != NRC_BF16)
       return set_error("batched caches compute in FP16 or BF16"), NRC_ERR_UNSUPPORTED;
+    if (caches[c]->cfg.width != 64 || caches[c]->cfg.path != NRC_PATH_FUSED)
+      return set_error("batched caches take the fused width-64 network"), NRC_ERR_UNSUPPORTED;
     if (caches[c]->cfg.optimizer != NRC_OPT_ADAM)
       return set_error("batched caches train with Adam"), NRC_ERR_UNSUPPORTED;
     if (!batch_same_cfg(caches[c]->cfg, caches[0]->cfg))

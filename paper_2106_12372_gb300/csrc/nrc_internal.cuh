@@ -234,6 +234,8 @@ cudaError_t launch_gather(const float* pool, const float* target, int64_t n_pool
 cudaError_t launch_encode(const float* rec, int64_t n, void* out, int out_dtype, int enc_mode, float pad,
                           cudaStream_t st);
 cudaError_t launch_infer_simt(Cache* c, const float* rec, int64_t n, float* rgb, cudaStream_t st);
+// Width-128 FP16 / BF16 queries on the tensor cores (k_tc128.cu).
+cudaError_t launch_infer_tc128(Cache* c, const float* rec, int64_t n, float* rgb, cudaStream_t st);
 cudaError_t launch_train_simt(Cache* c, const float* pool, const float* target, int64_t n_pool, int64_t batch,
                               uint64_t a, uint64_t cc, int step, int* n_partials, cudaStream_t st);
 cudaError_t launch_adam(Cache* c, int n_partials, float grad_scale, float* loss_out, cudaStream_t st);
@@ -454,6 +456,14 @@ __device__ __forceinline__ void load_record(const float* rec, int64_t row, float
 // in the 128-byte-swizzled layout.
 __host__ __device__ __forceinline__ uint32_t sw128_offset(uint32_t n, uint32_t k) {
   return (n >> 3) * 1024u + (n & 7u) * 128u + ((((k >> 3) ^ n) & 7u) << 4) + (k & 7u) * 2u;
+}
+
+// Byte offset of element (row n, input k) of matrix l in the 16-bit weight
+// image: matrices with more than 64 inputs are stored as blocks of 64
+// inputs (each block rows x 128 B, 128-byte swizzled), block after block.
+// For 64 inputs or fewer it is sw128_offset within the matrix.
+__host__ __device__ __forceinline__ uint32_t img_offset(const ImageShape& img, int l, uint32_t n, uint32_t k) {
+  return uint32_t(img.off[l]) + (k >> 6) * uint32_t(img.rows[l]) * 128u + sw128_offset(n, k & 63u);
 }
 
 // Programmatic dependent launch: a kernel launched with programmatic stream

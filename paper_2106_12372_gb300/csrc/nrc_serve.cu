@@ -252,6 +252,8 @@ nrc_status nrc_server_create(const nrc_server_config* cfg, const nrc_config* cac
     return set_error("nrc_server_create: configuration out of range"), NRC_ERR_INVALID_ARG;
   if (cache_cfg->dtype != NRC_FP16 && cache_cfg->dtype != NRC_BF16)
     return set_error("nrc_server_create: served caches compute in FP16 or BF16"), NRC_ERR_UNSUPPORTED;
+  if (cache_cfg->width != 64 || cache_cfg->path != NRC_PATH_FUSED)
+    return set_error("nrc_server_create: served caches take the fused width-64 network"), NRC_ERR_UNSUPPORTED;
   nrc_server* s = new (std::nothrow) nrc_server();
   if (!s) return set_error("host allocation failed"), NRC_ERR_OOM;
   s->cfg = *cfg;

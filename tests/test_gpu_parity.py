@@ -6,10 +6,10 @@ BF16 tensor-core path), per output, with the relative error floored at the
 batch rms (see parity.py for why the floor is needed).  BF16 does not meet
 2e-2 at every output: that bar is a known failure (xfail) and BF16 is held to
 it at the 99th percentile.  Every 16-bit result is also held, per element, to
-the tolerance of its format (error_bounds.format_tol: 2 |e| + 2 rms(e), e
+the tolerance of its format (error_bounds.format_tol: 2 |e| + c_N rms(e), e
 the error that exact FP16 / BF16 operand rounding of the oracle's arithmetic
-causes), and the GPU must sit closer to that rounding than the rounding sits
-to the FP64 result.
+causes, c_N the normal tail bound over the N compared elements), and the GPU
+must sit closer to that rounding than the rounding sits to the FP64 result.
 """
 import numpy as np
 import pytest
