@@ -3,6 +3,7 @@
     python -m paper_2106_12372_gb300.profile_case --what infer --n 2073600 --dtype fp16 --iters 3
     python -m paper_2106_12372_gb300.profile_case --what train --batch 16384 --dtype fp16 --iters 3
     python -m paper_2106_12372_gb300.profile_case --what frame --n 2073600 --steps 4 --iters 3
+    python -m paper_2106_12372_gb300.profile_case --what infer --net-width 128 --hidden 7 --dtype fp16
     python -m paper_2106_12372_gb300.profile_case --what paths --width 1920 --height 1080 --iters 3
 
 ``paths`` runs the training-record pipeline around the query (terminate, the
@@ -29,13 +30,15 @@ def main() -> None:
     ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--dtype", default="fp16")
     ap.add_argument("--iters", type=int, default=3)
+    ap.add_argument("--net-width", type=int, default=64, help="64, or 128 (with --hidden 7) for the wide network")
+    ap.add_argument("--hidden", type=int, default=5)
     args = ap.parse_args()
     build.build()
     dev = torch.device("cuda:0")
     if args.what == "paths":
         run_paths(args, dev)
         return
-    cache = nrc.Cache(dtype=args.dtype)
+    cache = nrc.Cache(dtype=args.dtype, width=args.net_width, hidden_layers=args.hidden)
     pool_np, tgt_np = synth.make_training_pool(args.batch * args.steps, seed=5)
     pool, tgt = torch.from_numpy(pool_np).to(dev), torch.from_numpy(tgt_np).to(dev)
     rec = torch.from_numpy(synth.make_records(args.n, seed=6)).to(dev) if args.what != "train" else None
