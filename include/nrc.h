@@ -277,7 +277,8 @@ NRC_API nrc_status nrc_batch_infer(nrc_batch* batch, const float* const* records
 /* One training step of every cache in one gradient launch and one Adam
  * launch: cache c trains on batch `step` of frame_seed[c]'s shuffle of its
  * pool (as nrc_train_step), batch[c] <= 65536 records (0 skips the cache).
- * The CTAs are shared out in proportion to the caches' batches.  All
+ * The CTAs (at most one per SM in all) are shared out so that the largest
+ * number of 128-record tiles any CTA trains is as small as possible.  All
  * arguments are host arrays of n_caches entries; pool[c], target[c] and
  * loss_out[c] (may be NULL, as may loss_out itself) are device pointers. */
 NRC_API nrc_status nrc_batch_train_step(nrc_batch* batch, const float* const* pool, const float* const* target,
@@ -303,7 +304,8 @@ NRC_API nrc_status nrc_batch_train_step_dev(nrc_batch* batch, const float* const
 NRC_API nrc_status nrc_batch_set_unit_tiles(nrc_batch* batch, int32_t unit_tiles);
 
 /* Training partition of nrc_batch_train_step.  0 (default): the CTAs (one
- * per SM in all) are shared out in proportion to the caches' batches.
+ * per SM in all) are shared out so that the largest number of tiles any CTA
+ * trains is as small as possible.
  * T > 0 (up to 4096): cache c gets ceil(tiles_c / T) CTAs, tiles_c = its
  * batch in 128-record tiles, whatever the other caches train; its weight
  * gradients are then summed in the same order as when it trains alone, so

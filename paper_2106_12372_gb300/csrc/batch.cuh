@@ -24,6 +24,8 @@ struct Batch {
   unsigned* d_counter = nullptr;
   TrainJob* d_jobs = nullptr;
   AdamJob* d_adam = nullptr;
+  TrainView* d_views = nullptr;   // training CTAs of the frame-kernel path (sm_count entries)
+  unsigned* d_tcounters = nullptr;  // its per-cache barrier counters + retire counter (max_caches + 1)
   float* d_partials = nullptr;
   // host: last uploaded query descriptors, pinned staging ring
   std::vector<BatchCache> h_caches;
@@ -31,6 +33,7 @@ struct Batch {
   // host: last uploaded training descriptors (zero-padded, compared bytewise)
   std::vector<TrainJob> h_jobs;
   std::vector<AdamJob> h_adam;
+  std::vector<TrainView> h_views;
   uint8_t* pinned = nullptr;
   size_t slot_bytes = 0;
   cudaEvent_t ev[kRing] = {};

@@ -149,15 +149,16 @@ __device__ __forceinline__ void train_grid_barrier(unsigned* ctr, unsigned targe
 }
 
 template <int MODE, bool BF16>
-__device__ __forceinline__ void frame_train(const FrameParams& p, uint8_t* sw, uint32_t tmem, uint64_t* bar_w,
+__device__ __forceinline__ void frame_train(const FrameParams& p, const TrainView& tv, uint8_t* sw, uint32_t tmem,
+                                            uint64_t* bar_w,
                                             uint64_t* bar_mma, uint64_t* bar_dw, uint64_t* bar_full,
                                             uint64_t* bar_free, float* red, const float* s_corr) {
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
-  const int b = blockIdx.x;
-  const int T = p.n_train;
+  const int b = tv.b;
+  const int T = tv.T;
   const int L = p.net.n_mats;
-  const int64_t tiles = (p.batch + kTile - 1) / kTile;
+  const int64_t tiles = (tv.batch + kTile - 1) / kTile;
   uint8_t* Hb = sw + ((p.img_bytes + 1023) & ~1023);
   float* aux = reinterpret_cast<float*>(Hb + kFrameBufs * 16384);  // [2][128][8]: target 3, factor 3
   const uint32_t hb_base = smem_u32(Hb), sw_base = smem_u32(sw);
@@ -167,6 +168,8 @@ __device__ __forceinline__ void frame_train(const FrameParams& p, uint8_t* sw, u
 
   if (warp > kIssuerWarp) {
     // ------------------------------------------------------------ producer
+    uint64_t sh_a = tv.a, sh_c = tv.c;
+    if (tv.seed) lcg_shuffle(tv.n_pool, *tv.seed, &sh_a, &sh_c);  // the frame seed lives on the device
     // three warps gather, encode and stage each tile's 128 rows (rows pt and
     // pt + 96), then arrive on the tile's full barrier
     const int pt = tid - (kIssuerWarp + 1) * 32;
@@ -178,14 +181,14 @@ __device__ __forceinline__ void frame_train(const FrameParams& p, uint8_t* sw, u
         for (int r = pt; r < kTile; r += kProducerThreads) {
           const int64_t row = i * kTile + r;
           float rec[kRecFloats], tg[3] = {0.f, 0.f, 0.f}, fac[3] = {1.f, 1.f, 1.f};
-          if (row < p.batch) {
-            const uint64_t idx = uint64_t(s) * uint64_t(p.batch) + uint64_t(row);
-            int64_t src = int64_t((p.a * idx + p.c) % uint64_t(p.n_pool));
-            if (!NRC_DCHECK(src >= 0 && src < p.n_pool, p.err)) src = 0;
-            load_record(p.pool, src, rec);
-            tg[0] = __ldg(p.target + src * 3);
-            tg[1] = __ldg(p.target + src * 3 + 1);
-            tg[2] = __ldg(p.target + src * 3 + 2);
+          if (row < tv.batch) {
+            const uint64_t idx = uint64_t(tv.step0 + s) * uint64_t(tv.batch) + uint64_t(row);
+            int64_t src = int64_t((sh_a * idx + sh_c) % uint64_t(tv.n_pool));
+            if (!NRC_DCHECK(src >= 0 && src < tv.n_pool, p.err)) src = 0;
+            load_record(tv.pool, src, rec);
+            tg[0] = __ldg(tv.target + src * 3);
+            tg[1] = __ldg(tv.target + src * 3 + 1);
+            tg[2] = __ldg(tv.target + src * 3 + 2);
             if (p.factor) {
 #pragma unroll
               for (int ch = 0; ch < 3; ++ch) fac[ch] = rec[8 + ch] + rec[11 + ch];
@@ -338,7 +341,7 @@ __device__ __forceinline__ void frame_train(const FrameParams& p, uint8_t* sw, u
   const int r = tid & 127;   // row == TMEM lane
   const uint32_t lane_base = uint32_t((warp & 3) * 32) << 16;
   const uint32_t t_acc = tmem + lane_base + uint32_t(16 * q);
-  const long long t0 = *p.t_ctr;
+  const long long t0 = *tv.t_ctr;
   uint32_t phase = 0;
   int j = 0;
   // one waiter per warp, then the warp's threads order their TMEM reads after it
@@ -369,7 +372,7 @@ __device__ __forceinline__ void frame_train(const FrameParams& p, uint8_t* sw, u
   // TMEM lanes 64..127 hold the same rows as 0..63 (the MMA's M = 128 reads
   // delta's 64 rows twice), so either half of the lanes can write a layer.
   const size_t stride = partial_stride(p.net.n_params);
-  float* P = p.partials + size_t(b) * stride;
+  float* P = tv.partials + size_t(b) * stride;
   auto write_dw = [&](int l) {
     const int R = p.net.dims[l + 1];
     const int o = r & 63;
@@ -390,7 +393,7 @@ __device__ __forceinline__ void frame_train(const FrameParams& p, uint8_t* sw, u
     if (tid == 0) {
       fence_proxy_async_global();
       mbar_arrive_expect_tx(bar_w, uint32_t(p.img_bytes));
-      bulk_g2s(sw, s == 0 ? p.img_in : p.img_work, uint32_t(p.img_bytes), bar_w);
+      bulk_g2s(sw, s == 0 ? tv.img_in : tv.img_work, uint32_t(p.img_bytes), bar_w);
     }
     float loss_acc = 0.0f;
     for (int64_t i = b; i < tiles; i += T, ++j) {
@@ -451,7 +454,7 @@ __device__ __forceinline__ void frame_train(const FrameParams& p, uint8_t* sw, u
         if ((tid & 31) == 0) mbar_wait(&bar_full[par], uint32_t((j >> 1) & 1), p.err);  // the staged targets
         __syncwarp();
         const float* ax = aux + (par * kTile + r) * 8;
-        const bool valid = i * kTile + r < p.batch;
+        const bool valid = i * kTile + r < tv.batch;
         const float fac[3] = {ax[3], ax[4], ax[5]};
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) y[ch] *= fac[ch];
@@ -542,10 +545,10 @@ __device__ __forceinline__ void frame_train(const FrameParams& p, uint8_t* sw, u
     auto load_state = [&](int Qp, int e) {
       pi = param_of(Qp, e, li);
       if (pi < p.net.n_params) {
-        w1 = __ldcg(p.w + pi);
-        m1 = __ldcg(p.m + pi);
-        v1 = __ldcg(p.v + pi);
-        if (p.ema) e1 = __ldcg(p.ema + pi);
+        w1 = __ldcg(tv.w + pi);
+        m1 = __ldcg(tv.m + pi);
+        v1 = __ldcg(tv.v + pi);
+        if (tv.ema) e1 = __ldcg(tv.ema + pi);
       }
     };
     const bool one_each = 4 * Qb <= kFrameCompute;
@@ -554,7 +557,7 @@ __device__ __forceinline__ void frame_train(const FrameParams& p, uint8_t* sw, u
     float4* st_state = reinterpret_cast<float4*>(Hb + 3 * 16384);  // [4][Qb], Qb <= 128
     if (one_each && tid < 4 * Qb) {
       const int a = tid / Qb, qd = tid % Qb;
-      const float* arr = a == 0 ? p.w : a == 1 ? p.m : a == 2 ? p.v : p.ema;
+      const float* arr = a == 0 ? tv.w : a == 1 ? tv.m : a == 2 ? tv.v : tv.ema;
       if (arr) {
         int l_unused;
         const int p0 = param_of(q_lo + qd, 0, l_unused);
@@ -565,17 +568,17 @@ __device__ __forceinline__ void frame_train(const FrameParams& p, uint8_t* sw, u
     cp_async_commit();
     fence_before();
     named_sync(kBarCompute, kFrameCompute);
-    if (tid == 0) P[p.net.n_params] = ((red[0] + red[1]) + (red[2] + red[3])) * p.inv3n;
-    train_grid_barrier(p.sync, unsigned(2 * s + 1) * unsigned(T), p.err, tid);
+    if (tid == 0) P[p.net.n_params] = ((red[0] + red[1]) + (red[2] + red[3])) * tv.inv3n;
+    train_grid_barrier(tv.bar, unsigned(2 * s + 1) * unsigned(T), p.err, tid);
 
     // the step's loss: the T partial sums, by one warp (lane k sums partials
     // k, k + 32, ... in order, then a fixed shuffle tree)
-    if (b == 0 && warp == kFrameCompute / 32 - 1 && p.loss_out) {
+    if (b == 0 && warp == kFrameCompute / 32 - 1 && tv.loss_out) {
       float sl = 0.0f;
-      for (int k = tid & 31; k < T; k += 32) sl += __ldcg(p.partials + size_t(k) * stride + p.net.n_params);
+      for (int k = tid & 31; k < T; k += 32) sl += __ldcg(tv.partials + size_t(k) * stride + p.net.n_params);
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) sl += __shfl_down_sync(0xffffffffu, sl, off);
-      if ((tid & 31) == 0) p.loss_out[s] = sl;
+      if ((tid & 31) == 0) tv.loss_out[s] = sl;
     }
     // ------------------------------------------------------ reduce + Adam
     // Thread (ch, qd) sums partials ch*C .. ch*C+C-1 of quad qd in order; the
@@ -587,7 +590,7 @@ __device__ __forceinline__ void frame_train(const FrameParams& p, uint8_t* sw, u
     float4* scratch = reinterpret_cast<float4*>(Hb + 2 * 16384);  // [NC][Qb] <= 8 KB, free between tiles
     if (one_each && tid < NC * Qb) {
       const int ch = tid / Qb, qd = tid % Qb;
-      const float* src = p.partials + size_t(q_lo + qd) * 4;
+      const float* src = tv.partials + size_t(q_lo + qd) * 4;
       const int k_lo = ch * C, k_hi = min(T, k_lo + C);
       float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
       for (int k0 = k_lo; k0 < k_hi; k0 += kSumBatch) {
@@ -610,28 +613,28 @@ __device__ __forceinline__ void frame_train(const FrameParams& p, uint8_t* sw, u
     cp_async_wait<0>();  // this thread's state quads have landed
     named_sync(kBarCompute, kFrameCompute);
     auto adam1 = [&](float g) {  // the loaded parameter's step (pi < n_params)
-      g *= p.inv3n;
+      g *= tv.inv3n;
       m1 = fmaf(p.b1, m1, (1.0f - p.b1) * g);
       v1 = fmaf(p.b2, v1, (1.0f - p.b2) * g * g);
       w1 = w1 - p.lr * (m1 / c1) / (sqrtf(v1 / c2) + p.eps);
-      p.w[pi] = w1;
-      p.m[pi] = m1;
-      p.v[pi] = v1;
+      tv.w[pi] = w1;
+      tv.m[pi] = m1;
+      tv.v[pi] = v1;
       const int qq = pi - p.net.w_off[li];
       uint32_t off = uint32_t(p.img.off[li]) + sw128_offset(uint32_t(qq / 64), uint32_t(qq % 64));
       if (!NRC_DCHECK(off + 2 <= uint32_t(p.img_bytes), p.err)) off = 0;
       if (BF16)
-        *reinterpret_cast<__nv_bfloat16*>(p.img_work + off) = __float2bfloat16_rn(w1);
+        *reinterpret_cast<__nv_bfloat16*>(tv.img_work + off) = __float2bfloat16_rn(w1);
       else
-        *reinterpret_cast<__half*>(p.img_work + off) = __float2half_rn(w1);
-      if (p.ema) {
+        *reinterpret_cast<__half*>(tv.img_work + off) = __float2half_rn(w1);
+      if (tv.ema) {
         // the weight average of Eq. 2 (bias-corrected reading); never read by training
         e1 = ((1.0f - p.alpha) * w1 + p.alpha * eta_prev * e1) / eta;
-        p.ema[pi] = e1;
+        tv.ema[pi] = e1;
         if (BF16)
-          *reinterpret_cast<__nv_bfloat16*>(p.img_ema_work + off) = __float2bfloat16_rn(e1);
+          *reinterpret_cast<__nv_bfloat16*>(tv.img_ema_work + off) = __float2bfloat16_rn(e1);
         else
-          *reinterpret_cast<__half*>(p.img_ema_work + off) = __float2half_rn(e1);
+          *reinterpret_cast<__half*>(tv.img_ema_work + off) = __float2half_rn(e1);
       }
     };
     if (one_each) {
@@ -641,7 +644,7 @@ __device__ __forceinline__ void frame_train(const FrameParams& p, uint8_t* sw, u
         w1 = sst[tid];
         m1 = sst[4 * Qb + tid];
         v1 = sst[8 * Qb + tid];
-        if (p.ema) e1 = sst[12 * Qb + tid];
+        if (tv.ema) e1 = sst[12 * Qb + tid];
       }
       if (tid < 4 * Qb && pi < p.net.n_params) {
         const float* sc = reinterpret_cast<const float*>(scratch);
@@ -654,14 +657,14 @@ __device__ __forceinline__ void frame_train(const FrameParams& p, uint8_t* sw, u
         load_state(q_lo + e / 4, e % 4);
         if (pi >= p.net.n_params) continue;
         float g = 0.0f;
-        for (int k = 0; k < T; ++k) g += __ldcg(p.partials + size_t(k) * stride + size_t(q_lo) * 4 + e);
+        for (int k = 0; k < T; ++k) g += __ldcg(tv.partials + size_t(k) * stride + size_t(q_lo) * 4 + e);
         adam1(g);
       }
     }
     fence_proxy_async_global();
-    if (s + 1 < p.n_steps) train_grid_barrier(p.sync, unsigned(2 * s + 2) * unsigned(T), p.err, tid);
+    if (s + 1 < p.n_steps) train_grid_barrier(tv.bar, unsigned(2 * s + 2) * unsigned(T), p.err, tid);
   }
-  if (b == 0 && tid == 0) *p.t_ctr = t0 + p.n_steps;
+  if (b == 0 && tid == 0) *tv.t_ctr = t0 + p.n_steps;
 }
 
 // The training's weight image (and weight-average image) over the cache's:
@@ -710,6 +713,31 @@ __global__ void __launch_bounds__(kFrameThreads, 1) k_frame_tc(const __grid_cons
     for (int s = 0; s < kSlots; ++s) mbar_init(&bar_q[s], 1);
     fence_barrier_init();
   }
+  TrainView tv;
+  if (trainer) {
+    tv.pool = p.pool;
+    tv.target = p.target;
+    tv.n_pool = p.n_pool;
+    tv.batch = p.batch;
+    tv.a = p.a;
+    tv.c = p.c;
+    tv.seed = nullptr;
+    tv.step0 = 0;
+    tv.T = p.n_train;
+    tv.b = int(blockIdx.x);
+    tv.w = p.w;
+    tv.m = p.m;
+    tv.v = p.v;
+    tv.ema = p.ema;
+    tv.t_ctr = p.t_ctr;
+    tv.img_in = p.img_in;
+    tv.img_work = p.img_work;
+    tv.img_ema_work = p.img_ema_work;
+    tv.partials = p.partials;
+    tv.bar = p.sync;
+    tv.loss_out = p.loss_out;
+    tv.inv3n = p.inv3n;
+  }
   if (trainer && tid < p.n_steps) {
     const long long t = *p.t_ctr + tid + 1;
     s_corr[4 * tid] = 1.0f - pow_int(p.b1, t);
@@ -730,7 +758,7 @@ __global__ void __launch_bounds__(kFrameThreads, 1) k_frame_tc(const __grid_cons
   fence_after();
   const uint32_t tmem = tmem_base_sh;
 
-  if (trainer) frame_train<MODE, BF16>(p, sw, tmem, &bar_w, &bar_mma, &bar_dw, bar_full, bar_free, red, s_corr);
+  if (trainer) frame_train<MODE, BF16>(p, tv, sw, tmem, &bar_w, &bar_mma, &bar_dw, bar_full, bar_free, red, s_corr);
 
   // ---------------------------------------------------------- query role
   const int64_t n_tiles = (p.n_q + kTile - 1) / kTile;
@@ -834,6 +862,144 @@ __global__ void __launch_bounds__(kFrameThreads, 1) k_frame_tc(const __grid_cons
     fence_after();
     tmem_dealloc(tmem, kTmemCols);
   }
+}
+
+// Batched training with the frame's training role: CTA blockIdx.x trains
+// views[blockIdx.x] (one cache of the batch; each cache has its own CTAs,
+// partials, barrier counter and weight image, so its result depends only on
+// its own partition).  counters[0 .. n_counters-2] are the caches' barrier
+// counters, counters[n_counters-1] counts retired CTAs; the last CTA zeroes
+// them all for the next launch.  Cooperative launch of at most one CTA per SM.
+template <int MODE, bool BF16>
+__global__ void __launch_bounds__(kFrameThreads, 1)
+    k_train_views(const __grid_constant__ FrameParams p, const TrainView* __restrict__ views, unsigned* counters,
+                  int n_counters) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ uint64_t bar_w, bar_mma, bar_dw, bar_full[2], bar_free[2];
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ float red[16];
+  __shared__ int s_last;
+  __shared__ float s_corr[4 * kFrameMaxSteps];
+  uint8_t* sw = align1024(smem_raw);
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  const TrainView tv = views[blockIdx.x];
+  if (warp == 0) {
+    tmem_alloc(&tmem_base_sh, kTmemCols);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    mbar_init(&bar_w, 1);
+    mbar_init(&bar_mma, 1);
+    mbar_init(&bar_dw, 1);
+    mbar_init(&bar_full[0], kProducerThreads);
+    mbar_init(&bar_full[1], kProducerThreads);
+    mbar_init(&bar_free[0], 1);
+    mbar_init(&bar_free[1], 1);
+    fence_barrier_init();
+  }
+  if (tid < p.n_steps) {
+    const long long t = *tv.t_ctr + tid + 1;
+    s_corr[4 * tid] = 1.0f - pow_int(p.b1, t);
+    s_corr[4 * tid + 1] = 1.0f - pow_int(p.b2, t);
+    s_corr[4 * tid + 2] = 1.0f - pow_int(p.alpha, t);
+    s_corr[4 * tid + 3] = 1.0f - pow_int(p.alpha, t - 1);
+  }
+  {
+    uint8_t* Hb = sw + ((p.img_bytes + 1023) & ~1023);
+    uint4* d = reinterpret_cast<uint4*>(Hb + 7 * 16384);
+    for (int k = tid; k < 1024; k += kFrameThreads) d[k] = make_uint4(0u, 0u, 0u, 0u);
+    fence_proxy_async_smem();
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_base_sh;
+  frame_train<MODE, BF16>(p, tv, sw, tmem, &bar_w, &bar_mma, &bar_dw, bar_full, bar_free, red, s_corr);
+  fence_before();
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    const unsigned old = atomicAdd(&counters[n_counters - 1], 1u);
+    s_last = old + 1 == gridDim.x;
+    if (s_last) __threadfence();
+  }
+  __syncthreads();
+  if (s_last) {
+    for (int k = tid; k < n_counters; k += kFrameThreads) counters[k] = 0u;
+    __threadfence();
+  }
+  if (warp == 0) {
+    fence_after();
+    tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+// Shared constants of a batched training launch: the configuration of the
+// batch's caches (all equal), n_steps steps, the first cache's error word.
+static void train_views_params(const Cache* proto, int n_steps, FrameParams* p) {
+  std::memset(p, 0, sizeof(*p));
+  p->n_steps = n_steps;
+  p->net = proto->net;
+  p->img = proto->img;
+  p->img_bytes = int(proto->img.off[proto->net.n_mats]);
+  p->pad = proto->cfg.pad_value;
+  p->loss_mode = proto->cfg.loss_mode;
+  p->loss_eps = proto->cfg.loss_eps;
+  p->factor = proto->cfg.refl_factor;
+  p->lr = proto->cfg.lr;
+  p->b1 = proto->cfg.beta1;
+  p->b2 = proto->cfg.beta2;
+  p->eps = proto->cfg.adam_eps;
+  p->alpha = proto->cfg.ema_alpha;
+  p->err = proto->err;
+}
+
+bool train_views_ok(const Cache* proto) {
+  const nrc_config& k = proto->cfg;
+  return k.path == NRC_PATH_FUSED && (k.dtype == NRC_FP16 || k.dtype == NRC_BF16) && k.optimizer == NRC_OPT_ADAM &&
+         k.width == 64 && proto->net.n_mats <= kFrameMaxMats;
+}
+
+cudaError_t launch_train_views(const Cache* proto, const TrainView* views, int n_views, unsigned* counters,
+                               int n_counters, int n_steps, cudaStream_t st) {
+  if (!train_views_ok(proto) || n_views < 1 || n_views > proto->sm_count || n_steps < 1 || n_steps > kFrameMaxSteps)
+    return cudaErrorInvalidValue;
+  FrameParams p;
+  train_views_params(proto, n_steps, &p);
+  const int align = 1024;
+  const int img_alloc = (p.img_bytes + 1023) & ~1023;
+  const int smem = img_alloc + kFrameBufs * 16384 + 2 * kTile * 8 * 4 + align;
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3(unsigned(n_views));
+  lc.blockDim = dim3(kFrameThreads);
+  lc.dynamicSmemBytes = size_t(smem);
+  lc.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  lc.attrs = attr;
+  lc.numAttrs = 1;
+  const bool bf16 = proto->cfg.dtype == NRC_BF16;
+  const int mode = proto->cfg.enc_mode;
+  cudaError_t e = cudaSuccess;
+  static std::atomic<int> attr_done[4];
+#define NRC_LAUNCH(M, B)                                                            \
+  e = ensure_smem(k_train_views<M, B>, smem, &attr_done[2 * (M) + ((B) ? 1 : 0)]); \
+  if (e != cudaSuccess) return e;                                                   \
+  e = cudaLaunchKernelEx(&lc, k_train_views<M, B>, p, views, counters, n_counters);  \
+  if (e != cudaSuccess) return e;
+  if (mode == 0 && !bf16) {
+    NRC_LAUNCH(0, false)
+  } else if (mode == 0 && bf16) {
+    NRC_LAUNCH(0, true)
+  } else if (!bf16) {
+    NRC_LAUNCH(1, false)
+  } else {
+    NRC_LAUNCH(1, true)
+  }
+#undef NRC_LAUNCH
+  return cudaGetLastError();
 }
 
 // Training CTAs of a frame: the split that minimises a model of the frame's

@@ -48,8 +48,11 @@ nrc_status batch_check(nrc_cache* const* caches, int n_caches) {
 
 static size_t slot_size(const Batch* b) {
   return up256(sizeof(BatchCache) * b->max_caches) + up256(sizeof(BatchUnit) * b->max_units) +
-         up256(sizeof(TrainJob) * b->max_jobs) + up256(sizeof(AdamJob) * b->max_caches);
+         up256(sizeof(TrainJob) * b->max_jobs) + up256(sizeof(AdamJob) * b->max_caches) +
+         up256(sizeof(TrainView) * b->max_jobs);
 }
+// where a ring slot keeps the training views
+static size_t views_offset(const Batch* b) { return slot_size(b) - up256(sizeof(TrainView) * b->max_jobs); }
 
 void batch_free(Batch* b) {
   cudaFree(b->d_caches);
@@ -57,6 +60,8 @@ void batch_free(Batch* b) {
   cudaFree(b->d_counter);
   cudaFree(b->d_jobs);
   cudaFree(b->d_adam);
+  cudaFree(b->d_views);
+  cudaFree(b->d_tcounters);
   cudaFree(b->d_partials);
   cudaFreeHost(b->pinned);
   for (int i = 0; i < kRing; ++i)
@@ -83,6 +88,9 @@ nrc_status batch_init(Batch* b, const nrc_cache* proto, int max_caches) {
   if (e == cudaSuccess) e = dev_alloc(&b->d_counter, sizeof(unsigned));
   if (e == cudaSuccess) e = dev_alloc(&b->d_jobs, sizeof(TrainJob) * b->max_jobs);
   if (e == cudaSuccess) e = dev_alloc(&b->d_adam, sizeof(AdamJob) * max_caches);
+  if (e == cudaSuccess) e = dev_alloc(&b->d_views, sizeof(TrainView) * b->max_jobs);
+  if (e == cudaSuccess) e = dev_alloc(&b->d_tcounters, sizeof(unsigned) * (max_caches + 1));
+  if (e == cudaSuccess) e = cudaMemset(b->d_tcounters, 0, sizeof(unsigned) * (max_caches + 1));
   if (e == cudaSuccess) e = dev_alloc(&b->d_partials, size_t(b->max_jobs) * b->stride * 4);
   if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&b->pinned), b->slot_bytes * kRing, cudaHostAllocDefault);
   for (int i = 0; i < kRing && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&b->ev[i], cudaEventDisableTiming);
@@ -102,14 +110,19 @@ static nrc_status reserve_jobs(Batch* b, int n_jobs, cudaStream_t st) {
   for (int i = 0; i < kRing && e == cudaSuccess; ++i) e = cudaEventSynchronize(b->ev[i]);
   if (e != cudaSuccess) return cuda_status(e, "batched training: growing the job buffers");
   cudaFree(b->d_jobs);
+  cudaFree(b->d_views);
   cudaFree(b->d_partials);
   cudaFreeHost(b->pinned);
   b->d_jobs = nullptr;
+  b->d_views = nullptr;
   b->d_partials = nullptr;
   b->pinned = nullptr;
+  b->h_jobs.clear();
+  b->h_views.clear();
   b->max_jobs = n_jobs;
   b->slot_bytes = slot_size(b);
   e = dev_alloc(&b->d_jobs, sizeof(TrainJob) * b->max_jobs);
+  if (e == cudaSuccess) e = dev_alloc(&b->d_views, sizeof(TrainView) * b->max_jobs);
   if (e == cudaSuccess) e = dev_alloc(&b->d_partials, size_t(b->max_jobs) * b->stride * 4);
   if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&b->pinned), b->slot_bytes * kRing, cudaHostAllocDefault);
   if (e != cudaSuccess) {
@@ -191,20 +204,93 @@ nrc_status batch_train_step(Batch* b, nrc_cache* const* caches, int nc, const fl
     }
     nrc_status s = reserve_jobs(b, used, st);
     if (s != NRC_OK) return s;
-  } else {  // CTAs per cache in proportion to its tiles (at least one each), at most one per SM in all
+  } else {
+    // CTAs per cache so that the largest number of tiles any CTA trains is as
+    // small as it can be with at most one CTA per SM in all: the smallest m
+    // with sum_c ceil(tiles_c / m) <= budget, then k_c = ceil(tiles_c / m)
     const int budget = std::max(nc, b->sm_count);
     nrc_status s = reserve_jobs(b, budget, st);
     if (s != NRC_OK) return s;
-    for (int c = 0; c < nc; ++c)
-      if (tiles[c]) {
-        k[c] = int(std::max<int64_t>(1, std::min<int64_t>(tiles[c], budget * tiles[c] / total)));
-        used += k[c];
-      }
-    while (used > budget) {  // trim the largest shares
-      int cmax = int(std::max_element(k.begin(), k.end()) - k.begin());
-      --k[cmax];
-      --used;
+    auto ctas_for = [&](int64_t m) {
+      int64_t sum = 0;
+      for (int c = 0; c < nc; ++c) sum += (tiles[c] + m - 1) / m;
+      return sum;
+    };
+    int64_t lo = 1, hi = *std::max_element(tiles.begin(), tiles.end());
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) / 2;
+      if (ctas_for(mid) <= budget)
+        hi = mid;
+      else
+        lo = mid + 1;
     }
+    for (int c = 0; c < nc; ++c) {
+      k[c] = int((tiles[c] + lo - 1) / lo);
+      used += k[c];
+    }
+  }
+  if (train_views_ok(caches[0]) && *std::max_element(k.begin(), k.end()) <= b->sm_count) {
+    // the frame kernel's training role: CTA q of cache c trains tiles q,
+    // q + k[c], ... of its batch and takes slice q of its parameters in the
+    // reduction and Adam.  One cooperative launch per run of whole caches
+    // whose CTAs fit one per SM, so a cache's arithmetic never depends on
+    // the others.  (Views zero-initialised, compared byte for byte with the
+    // last upload.)
+    std::vector<TrainView> hv(static_cast<size_t>(used));
+    int jv = 0;
+    for (int c = 0; c < nc; ++c) {
+      if (!tiles[c]) continue;
+      nrc_cache* cc = caches[c];
+      uint64_t a = 0, ic = 0;
+      if (!seed_dev) lcg_params(n_pool[c], frame_seed[c], &a, &ic);
+      const int j0 = jv;
+      for (int q = 0; q < k[c]; ++q, ++jv) {
+        TrainView& V = hv[size_t(jv)];
+        V.pool = pool[c];
+        V.target = target[c];
+        V.n_pool = n_pool[c];
+        V.batch = batch[c];
+        V.a = a;
+        V.c = ic;
+        V.seed = seed_dev ? seed_dev + c : nullptr;
+        V.step0 = step;
+        V.T = k[c];
+        V.b = q;
+        V.w = cc->w;
+        V.m = cc->m;
+        V.v = cc->v;
+        V.ema = cc->cfg.ema ? cc->ema : nullptr;
+        V.t_ctr = cc->t;
+        V.img_in = cc->wimg;
+        V.img_work = cc->wimg;
+        V.img_ema_work = cc->cfg.ema ? cc->wimg_ema : nullptr;
+        V.partials = b->d_partials + size_t(j0) * b->stride;
+        V.bar = b->d_tcounters + c;
+        V.loss_out = loss_out ? loss_out[c] : nullptr;
+        V.inv3n = float(1.0 / (3.0 * double(batch[c])));
+      }
+    }
+    cudaError_t e = cudaSuccess;
+    if (hv.size() != b->h_views.size() || std::memcmp(hv.data(), b->h_views.data(), sizeof(TrainView) * hv.size())) {
+      int slot;
+      uint8_t* h = ring_slot(b, &slot) + views_offset(b);
+      std::memcpy(h, hv.data(), sizeof(TrainView) * hv.size());
+      e = cudaMemcpyAsync(b->d_views, h, sizeof(TrainView) * hv.size(), cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = cudaEventRecord(b->ev[slot], st);
+      if (e != cudaSuccess) return cuda_status(e, "batched training");
+      b->h_views.swap(hv);
+    }
+    int first = 0, run = 0;
+    for (int c = 0; c <= nc && e == cudaSuccess; ++c) {
+      if (c == nc || run + k[c] > b->sm_count) {
+        if (run > 0) e = launch_train_views(caches[0], b->d_views + first, run, b->d_tcounters, nc + 1, 1, st);
+        first += run;
+        run = 0;
+      }
+      if (c < nc) run += k[c];
+    }
+    for (int c = 0; c < nc; ++c) caches[c]->launches += 1;
+    return cuda_status(e, "batched training");
   }
   // descriptors in zero-initialised vectors (padding included), so that an
   // unchanged call compares equal to the last upload byte for byte

@@ -234,6 +234,40 @@ cudaError_t launch_gather(const float* pool, const float* target, int64_t n_pool
 cudaError_t launch_encode(const float* rec, int64_t n, void* out, int out_dtype, int enc_mode, float pad,
                           cudaStream_t st);
 cudaError_t launch_infer_simt(Cache* c, const float* rec, int64_t n, float* rgb, cudaStream_t st);
+// What one training CTA trains: its cache's data, state and images, and its
+// place among the cache's T training CTAs (b), with the cache's own grid
+// barrier counter.  The frame kernel's training CTAs all train the frame's
+// cache; a batched training launch gives each CTA one cache of the batch.
+struct TrainView {
+  const float* pool;
+  const float* target;
+  int64_t n_pool;
+  int64_t batch;
+  uint64_t a, c;          // the shuffle (Sec. 3.5)
+  const uint64_t* seed;   // device: the frame seed to derive a, c from (null: as given)
+  int step0;              // index of the first step (its batch of the shuffle)
+  int T, b;
+  float* w;
+  float* m;
+  float* v;
+  float* ema;             // null: no weight average
+  long long* t_ctr;
+  const uint8_t* img_in;  // image of the weights the first step starts from
+  uint8_t* img_work;      // the image every step writes
+  uint8_t* img_ema_work;
+  float* partials;        // [T][partial_stride]
+  unsigned* bar;          // the T CTAs' grid barrier counter
+  float* loss_out;
+  float inv3n;
+};
+
+// Batched training with the frame kernel's training role (k_frame.cu): one
+// cooperative launch of n_views <= SM-count CTAs, CTA k training views[k]
+// (device array) for n_steps steps; counters: n_counters - 1 barrier
+// counters (the views' bar) and a retire counter, zero at launch and left zero.
+bool train_views_ok(const Cache* proto);
+cudaError_t launch_train_views(const Cache* proto, const TrainView* views, int n_views, unsigned* counters,
+                               int n_counters, int n_steps, cudaStream_t st);
 // Width-128 FP16 / BF16 queries on the tensor cores (k_tc128.cu).
 cudaError_t launch_infer_tc128(Cache* c, const float* rec, int64_t n, float* rgb, cudaStream_t st);
 cudaError_t launch_train_simt(Cache* c, const float* pool, const float* target, int64_t n_pool, int64_t batch,
