@@ -188,3 +188,18 @@ def format_tol(err, dims=None):
         out[off:off + n] = 2.0 * e + tail_factor(n) * np.sqrt(np.mean(e ** 2))
         off += n
     return out
+
+
+def format_check(got, ref, emul, dims=None, label="", model_check=True):
+    """Asserts |got - ref| <= format_tol(emul - ref) at every element and, with
+    model_check, rms(got - emul) <= rms(emul - ref) / 2; returns the worst
+    ratio to the tolerance and that rms ratio."""
+    got, ref, emul = (np.asarray(a, np.float64).ravel() for a in (got, ref, emul))
+    e = emul - ref
+    worst = float(np.max(np.abs(got - ref) / format_tol(e, dims)))
+    model = float(np.sqrt(np.mean((got - emul) ** 2)) / np.sqrt(np.mean(e ** 2)))
+    print("format bound", label, "max |err| / tol", worst, "rms(gpu - rounding) / rms(rounding error)", model)
+    assert worst <= 1.0, (label, worst)
+    if model_check:
+        assert model <= 0.5, (label, model)
+    return worst, model

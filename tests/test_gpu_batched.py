@@ -12,6 +12,7 @@ import pytest
 
 from paper_2106_12372_gb300 import synth
 from parity import rel_err, stats
+import error_bounds as EB
 
 pytestmark = pytest.mark.gpu
 
@@ -129,6 +130,10 @@ def test_batch_train_step_matches_oracle():
         assert t == 1
         assert abs(losses[k].item() - ref_loss) <= 2e-2 * abs(ref_loss)
         assert np.linalg.norm(g - ref_g) <= 2e-2 * np.linalg.norm(ref_g)
+        # and per element, the format tolerance of the batch the cache trained on
+        rec, tg, _ = O.gather(pools[k], tgts[k], batches[k], fss[k], 2)
+        emul = EB.emulate_16bit(synth.xavier_weights(DIMS, seed=700 + k), DIMS, O.encode(rec), tg, "fp16")[1]
+        EB.format_check(g, ref_g, emul, DIMS, label=f"batched train {k}")
         c.check_error()
 
 

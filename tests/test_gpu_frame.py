@@ -24,6 +24,7 @@ import pytest
 
 from paper_2106_12372_gb300 import synth
 from parity import rel_err, stats
+import error_bounds as EB
 
 pytestmark = pytest.mark.gpu
 
@@ -167,6 +168,10 @@ def test_fused_frame_against_oracle(dtype):
     assert nq <= 2e-2 and ng <= 2e-2
     if dtype == "fp16":
         assert e.max() <= 2e-2 and eg.max() <= 2e-2, (e.max(), eg.max())
+    # per element, both dtypes: the format tolerance (queries and the step's gradient)
+    EB.format_check(rgb.cpu().numpy(), ref_rgb, EB.emulate_infer(w0, DIMS, O.encode(q), dtype), label=f"frame queries {dtype}")
+    rec, tg, _ = O.gather(pool, tgt, 16384, fs, 0)
+    EB.format_check(g, ref_g, EB.emulate_16bit(w0, DIMS, O.encode(rec), tg, dtype)[1], DIMS, label=f"frame gradient {dtype}")
     # three more steps: each step's loss against the oracle's on the same weights trajectory is chaotic
     # beyond the first steps; the first four are held to 5e-2
     losses = torch.zeros(4, device=DEV)

@@ -96,13 +96,7 @@ def test_loss_curve_follows_the_oracle():
 
 
 def _format_check(got, ref, emul, label, model_check=True):
-    e = emul - ref
-    worst = float(np.max(np.abs(got - ref) / EB.format_tol(e)))
-    model = float(np.sqrt(np.mean((got - emul) ** 2)) / np.sqrt(np.mean(e ** 2)))
-    print("width 128 format bound", label, "max |err| / tol", worst, "rms(gpu - rounding) / rms(rounding error)", model)
-    assert worst <= 1.0, (label, worst)
-    if model_check:
-        assert model <= 0.5, (label, model)
+    EB.format_check(got, ref, emul, label="width 128 " + label, model_check=model_check)
 
 
 @pytest.mark.parametrize("dtype", ["fp16", "bf16"])
