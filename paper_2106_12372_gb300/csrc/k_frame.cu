@@ -93,6 +93,7 @@ struct FrameParams {
   uint8_t* img_ema_out;
   float* partials;           // [T][partial_stride]
   unsigned* sync;            // [0] grid barrier, [1] query tile tickets, [2] retired CTAs, [3] CTAs holding the old image
+  TrainView tv;              // the frame's training, as the training role reads it (b unused: blockIdx.x)
   NetShape net;
   ImageShape img;
   int img_bytes;
@@ -149,13 +150,12 @@ __device__ __forceinline__ void train_grid_barrier(unsigned* ctr, unsigned targe
 }
 
 template <int MODE, bool BF16>
-__device__ __forceinline__ void frame_train(const FrameParams& p, const TrainView& tv, uint8_t* sw, uint32_t tmem,
-                                            uint64_t* bar_w,
+__device__ __forceinline__ void frame_train(const FrameParams& p, const TrainView& tv, const int b, uint8_t* sw,
+                                            uint32_t tmem, uint64_t* bar_w,
                                             uint64_t* bar_mma, uint64_t* bar_dw, uint64_t* bar_full,
                                             uint64_t* bar_free, float* red, const float* s_corr) {
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
-  const int b = tv.b;
   const int T = tv.T;
   const int L = p.net.n_mats;
   const int64_t tiles = (tv.batch + kTile - 1) / kTile;
@@ -713,31 +713,6 @@ __global__ void __launch_bounds__(kFrameThreads, 1) k_frame_tc(const __grid_cons
     for (int s = 0; s < kSlots; ++s) mbar_init(&bar_q[s], 1);
     fence_barrier_init();
   }
-  TrainView tv;
-  if (trainer) {
-    tv.pool = p.pool;
-    tv.target = p.target;
-    tv.n_pool = p.n_pool;
-    tv.batch = p.batch;
-    tv.a = p.a;
-    tv.c = p.c;
-    tv.seed = nullptr;
-    tv.step0 = 0;
-    tv.T = p.n_train;
-    tv.b = int(blockIdx.x);
-    tv.w = p.w;
-    tv.m = p.m;
-    tv.v = p.v;
-    tv.ema = p.ema;
-    tv.t_ctr = p.t_ctr;
-    tv.img_in = p.img_in;
-    tv.img_work = p.img_work;
-    tv.img_ema_work = p.img_ema_work;
-    tv.partials = p.partials;
-    tv.bar = p.sync;
-    tv.loss_out = p.loss_out;
-    tv.inv3n = p.inv3n;
-  }
   if (trainer && tid < p.n_steps) {
     const long long t = *p.t_ctr + tid + 1;
     s_corr[4 * tid] = 1.0f - pow_int(p.b1, t);
@@ -758,7 +733,9 @@ __global__ void __launch_bounds__(kFrameThreads, 1) k_frame_tc(const __grid_cons
   fence_after();
   const uint32_t tmem = tmem_base_sh;
 
-  if (trainer) frame_train<MODE, BF16>(p, tv, sw, tmem, &bar_w, &bar_mma, &bar_dw, bar_full, bar_free, red, s_corr);
+  if (trainer)
+    frame_train<MODE, BF16>(p, p.tv, int(blockIdx.x), sw, tmem, &bar_w, &bar_mma, &bar_dw, bar_full, bar_free, red,
+                            s_corr);
 
   // ---------------------------------------------------------- query role
   const int64_t n_tiles = (p.n_q + kTile - 1) / kTile;
@@ -915,7 +892,7 @@ __global__ void __launch_bounds__(kFrameThreads, 1)
   __syncthreads();
   fence_after();
   const uint32_t tmem = tmem_base_sh;
-  frame_train<MODE, BF16>(p, tv, sw, tmem, &bar_w, &bar_mma, &bar_dw, bar_full, bar_free, red, s_corr);
+  frame_train<MODE, BF16>(p, tv, tv.b, sw, tmem, &bar_w, &bar_mma, &bar_dw, bar_full, bar_free, red, s_corr);
   fence_before();
   __syncthreads();
   if (tid == 0) {
@@ -1100,6 +1077,29 @@ cudaError_t launch_frame_tc(Cache* c, const float* rec, int64_t n_q, float* rgb,
   p.eps = c->cfg.adam_eps;
   p.alpha = c->cfg.ema_alpha;
   p.err = c->err;
+  TrainView& tv = p.tv;
+  tv.pool = p.pool;
+  tv.target = p.target;
+  tv.n_pool = p.n_pool;
+  tv.batch = p.batch;
+  tv.a = p.a;
+  tv.c = p.c;
+  tv.seed = nullptr;
+  tv.step0 = 0;
+  tv.T = p.n_train;
+  tv.b = 0;
+  tv.w = p.w;
+  tv.m = p.m;
+  tv.v = p.v;
+  tv.ema = p.ema;
+  tv.t_ctr = p.t_ctr;
+  tv.img_in = p.img_in;
+  tv.img_work = p.img_work;
+  tv.img_ema_work = p.img_ema_work;
+  tv.partials = p.partials;
+  tv.bar = p.sync;
+  tv.loss_out = p.loss_out;
+  tv.inv3n = p.inv3n;
   const int align = 1024;
   const int img_alloc = (p.img_bytes + 1023) & ~1023;
   const int smem_train = img_alloc + kFrameBufs * 16384 + 2 * kTile * 8 * 4 + align;
