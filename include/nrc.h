@@ -265,9 +265,11 @@ NRC_API nrc_status nrc_batch_destroy(nrc_batch* batch);
 /* Cache queries of every cache in ONE persistent launch (Sec. 4's fused
  * network per cache): rgb[c][n[c]][3] = MLP_c(encode(records[c][n[c]][16])).
  * records, n and rgb are host arrays of n_caches entries; records[c] and
- * rgb[c] are device pointers as in nrc_infer.  The work is cut into units of
- * up to unit_tiles 128-row tiles of one cache, taken by the CTAs from a
- * device counter; each row is computed exactly as nrc_infer computes it.
+ * rgb[c] are device pointers as in nrc_infer.  With unit_tiles 0 (the
+ * default) each CTA takes one contiguous range of all the caches' 128-row
+ * tiles (cache after cache, equal counts); otherwise the work is cut into
+ * units of up to unit_tiles tiles of one cache, taken by the CTAs from a
+ * device counter.  Each row is computed exactly as nrc_infer computes it.
  * Descriptors are uploaded (asynchronously) only when they differ from the
  * previous call's, so the launch can be captured in a CUDA graph and
  * replayed for the same buffers. */
@@ -300,7 +302,8 @@ NRC_API nrc_status nrc_batch_train_step_dev(nrc_batch* batch, const float* const
                                             const uint64_t* frame_seed_dev, int32_t step, float* const* loss_out,
                                             nrc_stream stream);
 
-/* Sets the work-unit size of nrc_batch_infer (1 .. 4096 tiles; default 20). */
+/* Sets the work-unit size of nrc_batch_infer (1 .. 4096 tiles; 0, the
+ * default: one contiguous range per CTA). */
 NRC_API nrc_status nrc_batch_set_unit_tiles(nrc_batch* batch, int32_t unit_tiles);
 
 /* Training partition of nrc_batch_train_step.  0 (default): the CTAs (one
@@ -313,7 +316,7 @@ NRC_API nrc_status nrc_batch_set_unit_tiles(nrc_batch* batch, int32_t unit_tiles
 NRC_API nrc_status nrc_batch_set_train_tiles(nrc_batch* batch, int32_t train_tiles);
 
 /* Autotuner: runs nrc_batch_infer on the given buffers with each candidate
- * work-unit size (5 .. 160 tiles), keeps the fastest (CUDA-event timing; it
+ * work-unit size (0 and 5 .. 160 tiles), keeps the fastest (CUDA-event timing; it
  * synchronises the stream) and reports it in *chosen (may be NULL). */
 NRC_API nrc_status nrc_batch_autotune(nrc_batch* batch, const float* const* records, const int64_t* n,
                                       float* const* rgb, nrc_stream stream, int32_t* chosen);
@@ -349,7 +352,7 @@ typedef struct nrc_server_config {
   int32_t train_steps;    /* training steps per frame (default 4) */
   int32_t train_batch;    /* records per training step (default 16384, <= 65536) */
   int32_t train_tiles;    /* 128-record tiles per training CTA (default 4) */
-  int32_t unit_tiles;     /* 128-row tiles per query work unit (default 20) */
+  int32_t unit_tiles;     /* 128-row tiles per query work unit (default 0: one contiguous range per CTA) */
 } nrc_server_config;
 
 /* One finished frame.  Times are CLOCK_MONOTONIC nanoseconds (nrc_now_ns). */

@@ -13,7 +13,7 @@ constexpr int kRing = 8;  // pinned descriptor slots in flight
 
 struct Batch {
   std::vector<nrc_cache*> caches;  // the caches of the nrc_batch C object (unused by the server)
-  int unit_tiles = 20;             // 128-row tiles per query work unit
+  int unit_tiles = 0;              // 128-row tiles per query work unit; 0: one contiguous range per CTA
   int train_tiles = 0;             // >0: a cache's training CTAs = ceil(its tiles / train_tiles)
   int max_caches = 0;
   int max_units = 0;
@@ -25,11 +25,13 @@ struct Batch {
   TrainJob* d_jobs = nullptr;
   AdamJob* d_adam = nullptr;
   TrainView* d_views = nullptr;   // training CTAs of the frame-kernel path (sm_count entries)
+  int* d_uoff = nullptr;           // static query ranges: first unit of each CTA (sm_count + 1 entries)
   unsigned* d_tcounters = nullptr;  // its per-cache barrier counters + retire counter (max_caches + 1)
   float* d_partials = nullptr;
   // host: last uploaded query descriptors, pinned staging ring
   std::vector<BatchCache> h_caches;
   std::vector<BatchUnit> h_units;
+  std::vector<int> h_uoff;
   // host: last uploaded training descriptors (zero-padded, compared bytewise)
   std::vector<TrainJob> h_jobs;
   std::vector<AdamJob> h_adam;

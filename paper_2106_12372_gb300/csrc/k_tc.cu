@@ -43,7 +43,8 @@ struct BatchInferParams {
   const BatchCache* caches;
   const BatchUnit* units;
   int n_units;
-  unsigned* counter;  // work-unit counter, zero at launch
+  unsigned* counter;      // work-unit counter, zero at launch
+  const int* unit_off;    // static ranges: CTA b runs units unit_off[b] .. unit_off[b+1]-1 (null: the counter)
   int img_bytes;
   int n_mats;
   ImageShape img;
@@ -177,13 +178,10 @@ __global__ void __launch_bounds__(kInferThreads, 1) k_infer_batched(const __grid
   rs.rot = uint32_t((rit >> 1) & 3);
   int cur = -1;
   uint32_t wphase = 0, phase = 0;
-  while (true) {
-    __syncthreads();  // every slot is done with the previous unit (its MMAs completed)
-    if (tid == 0) unit_sh = int(atomicAdd(p.counter, 1u));
-    __syncthreads();
-    const int u = unit_sh;
-    if (u >= p.n_units) break;
-    const BatchUnit U = p.units[u];
+  // one unit's tiles, interleaved over the slots; the weight image is loaded
+  // when the unit's cache differs from the last one (every slot is done with
+  // the previous unit then: the callers synchronise the CTA first)
+  auto run_unit = [&](const BatchUnit& U) {
     const BatchCache C = p.caches[U.cache];
     if (U.cache != cur) {
       if (tid == 0) {
@@ -214,6 +212,24 @@ __global__ void __launch_bounds__(kInferThreads, 1) k_infer_batched(const __grid
                         row < C.n ? C.rgb + row * 3 : nullptr, fac_row, rs.rot);
     }
     cp_async_wait<0>();
+  };
+  if (p.unit_off) {
+    // static: this CTA's contiguous range of the tiles, cache after cache
+    // (consecutive units of a CTA belong to different caches)
+    const int u1 = p.unit_off[blockIdx.x + 1];
+    for (int u = p.unit_off[blockIdx.x]; u < u1; ++u) {
+      __syncthreads();  // every slot is done with the previous unit (its MMAs completed)
+      run_unit(p.units[u]);
+    }
+  } else {
+    while (true) {
+      __syncthreads();  // every slot is done with the previous unit (its MMAs completed)
+      if (tid == 0) unit_sh = int(atomicAdd(p.counter, 1u));
+      __syncthreads();
+      const int u = unit_sh;
+      if (u >= p.n_units) break;
+      run_unit(p.units[u]);
+    }
   }
   fence_before();
   __syncthreads();
@@ -490,12 +506,13 @@ cudaError_t launch_infer_tc(Cache* c, const float* rec, int64_t n, float* rgb, c
 }
 
 cudaError_t launch_infer_batched(const Cache* proto, const BatchCache* caches, const BatchUnit* units, int n_units,
-                                 unsigned* counter, int grid, cudaStream_t st) {
+                                 unsigned* counter, int grid, cudaStream_t st, const int* unit_off) {
   BatchInferParams p;
   p.caches = caches;
   p.units = units;
   p.n_units = n_units;
   p.counter = counter;
+  p.unit_off = unit_off;
   p.img_bytes = proto->img.off[proto->net.n_mats];
   p.n_mats = proto->net.n_mats;
   p.img = proto->img;
@@ -505,7 +522,7 @@ cudaError_t launch_infer_batched(const Cache* proto, const BatchCache* caches, c
   const int smem = ((p.img_bytes + 1023) & ~1023) + kSlots * 2 * 8192 + 1024;
   const bool bf16 = proto->cfg.dtype == NRC_BF16;
   const int mode = proto->cfg.enc_mode;
-  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), st);
+  cudaError_t e = unit_off ? cudaSuccess : cudaMemsetAsync(counter, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   static std::atomic<int> attr_done[4];
 #define NRC_LAUNCH(M, B)                                                        \

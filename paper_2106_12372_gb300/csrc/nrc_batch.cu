@@ -49,7 +49,12 @@ nrc_status batch_check(nrc_cache* const* caches, int n_caches) {
 static size_t slot_size(const Batch* b) {
   return up256(sizeof(BatchCache) * b->max_caches) + up256(sizeof(BatchUnit) * b->max_units) +
          up256(sizeof(TrainJob) * b->max_jobs) + up256(sizeof(AdamJob) * b->max_caches) +
-         up256(sizeof(TrainView) * b->max_jobs);
+         up256(sizeof(int) * (b->sm_count + 1)) + up256(sizeof(TrainView) * b->max_jobs);
+}
+// where a ring slot keeps the static query ranges' unit offsets
+static size_t uoff_offset(const Batch* b) {
+  return up256(sizeof(BatchCache) * b->max_caches) + up256(sizeof(BatchUnit) * b->max_units) +
+         up256(sizeof(TrainJob) * b->max_jobs) + up256(sizeof(AdamJob) * b->max_caches);
 }
 // where a ring slot keeps the training views
 static size_t views_offset(const Batch* b) { return slot_size(b) - up256(sizeof(TrainView) * b->max_jobs); }
@@ -61,6 +66,7 @@ void batch_free(Batch* b) {
   cudaFree(b->d_jobs);
   cudaFree(b->d_adam);
   cudaFree(b->d_views);
+  cudaFree(b->d_uoff);
   cudaFree(b->d_tcounters);
   cudaFree(b->d_partials);
   cudaFreeHost(b->pinned);
@@ -89,6 +95,7 @@ nrc_status batch_init(Batch* b, const nrc_cache* proto, int max_caches) {
   if (e == cudaSuccess) e = dev_alloc(&b->d_jobs, sizeof(TrainJob) * b->max_jobs);
   if (e == cudaSuccess) e = dev_alloc(&b->d_adam, sizeof(AdamJob) * max_caches);
   if (e == cudaSuccess) e = dev_alloc(&b->d_views, sizeof(TrainView) * b->max_jobs);
+  if (e == cudaSuccess) e = dev_alloc(&b->d_uoff, sizeof(int) * (b->sm_count + 1));
   if (e == cudaSuccess) e = dev_alloc(&b->d_tcounters, sizeof(unsigned) * (max_caches + 1));
   if (e == cudaSuccess) e = cudaMemset(b->d_tcounters, 0, sizeof(unsigned) * (max_caches + 1));
   if (e == cudaSuccess) e = dev_alloc(&b->d_partials, size_t(b->max_jobs) * b->stride * 4);
@@ -145,13 +152,41 @@ nrc_status batch_infer(Batch* b, nrc_cache* const* caches, int nc, const float* 
     if (n[c] > (int64_t(1) << 38)) return set_error("batched query: n[%d] too large", c), NRC_ERR_INVALID_ARG;
     hc[c] = BatchCache{query_image(caches[c]), records[c], rgb[c], n[c]};
     const int64_t tiles = (n[c] + kTile - 1) / kTile;
-    for (int64_t t = 0; t < tiles; t += b->unit_tiles)
-      hu.push_back(BatchUnit{c, int(t), int(std::min<int64_t>(tiles, t + b->unit_tiles))});
+    if (b->unit_tiles > 0)
+      for (int64_t t = 0; t < tiles; t += b->unit_tiles)
+        hu.push_back(BatchUnit{c, int(t), int(std::min<int64_t>(tiles, t + b->unit_tiles))});
+  }
+  // static ranges (unit_tiles 0): CTA g takes tiles [g T / G, (g + 1) T / G)
+  // of all the caches' tiles in order, cut where a cache ends
+  std::vector<int> hoff;
+  int grid_static = 0;
+  if (b->unit_tiles == 0) {
+    int64_t total = 0;
+    std::vector<int64_t> first(static_cast<size_t>(nc) + 1, 0);
+    for (int c = 0; c < nc; ++c) {
+      first[size_t(c)] = total;
+      total += (n[c] + kTile - 1) / kTile;
+    }
+    first[size_t(nc)] = total;
+    grid_static = int(std::min<int64_t>(b->sm_count, (total + kQuerySlots - 1) / kQuerySlots));
+    int c = 0;
+    for (int g = 0; g < grid_static; ++g) {
+      hoff.push_back(int(hu.size()));
+      const int64_t lo = total * g / grid_static, hi = total * (g + 1) / grid_static;
+      int64_t t = lo;
+      while (t < hi) {
+        while (first[size_t(c) + 1] <= t) ++c;
+        const int64_t end = std::min(hi, first[size_t(c) + 1]);
+        hu.push_back(BatchUnit{c, int(t - first[size_t(c)]), int(end - first[size_t(c)])});
+        t = end;
+      }
+    }
+    hoff.push_back(int(hu.size()));
   }
   if (hu.empty()) return NRC_OK;
   if (int(hu.size()) > b->max_units) return set_error("batched query: too many work units"), NRC_ERR_INVALID_ARG;
   cudaError_t e = cudaSuccess;
-  const bool same = hc.size() == b->h_caches.size() && hu.size() == b->h_units.size() &&
+  const bool same = hc.size() == b->h_caches.size() && hu.size() == b->h_units.size() && hoff == b->h_uoff &&
                     !std::memcmp(hc.data(), b->h_caches.data(), sizeof(BatchCache) * hc.size()) &&
                     !std::memcmp(hu.data(), b->h_units.data(), sizeof(BatchUnit) * hu.size());
   if (!same) {  // descriptors are uploaded only when they change (a replayed graph reuses them)
@@ -162,13 +197,20 @@ nrc_status batch_infer(Batch* b, nrc_cache* const* caches, int nc, const float* 
     std::memcpy(hu_p, hu.data(), sizeof(BatchUnit) * hu.size());
     e = cudaMemcpyAsync(b->d_caches, h, sizeof(BatchCache) * nc, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_units, hu_p, sizeof(BatchUnit) * hu.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !hoff.empty()) {
+      int* ho = reinterpret_cast<int*>(h + uoff_offset(b));
+      std::memcpy(ho, hoff.data(), sizeof(int) * hoff.size());
+      e = cudaMemcpyAsync(b->d_uoff, ho, sizeof(int) * hoff.size(), cudaMemcpyHostToDevice, st);
+    }
     if (e == cudaSuccess) e = cudaEventRecord(b->ev[slot], st);
     if (e != cudaSuccess) return cuda_status(e, "batched query: descriptor upload");
     b->h_caches = hc;
     b->h_units = hu;
+    b->h_uoff = hoff;
   }
-  const int grid = std::min<int>(b->sm_count, int(hu.size()));
-  e = launch_infer_batched(caches[0], b->d_caches, b->d_units, int(hu.size()), b->d_counter, grid, st);
+  const int grid = b->unit_tiles == 0 ? grid_static : std::min<int>(b->sm_count, int(hu.size()));
+  e = launch_infer_batched(caches[0], b->d_caches, b->d_units, int(hu.size()), b->d_counter, grid, st,
+                           b->unit_tiles == 0 ? b->d_uoff : nullptr);
   for (int c = 0; c < nc; ++c) caches[c]->launches += 1;
   return cuda_status(e, "batched query");
 }
@@ -396,7 +438,7 @@ nrc_status nrc_batch_destroy(nrc_batch* b) {
 }
 
 nrc_status nrc_batch_set_unit_tiles(nrc_batch* b, int32_t unit_tiles) {
-  if (!b || unit_tiles < 1 || unit_tiles > 4096) return set_error("unit_tiles must be in [1, 4096]"), NRC_ERR_INVALID_ARG;
+  if (!b || unit_tiles < 0 || unit_tiles > 4096) return set_error("unit_tiles must be in [0, 4096]"), NRC_ERR_INVALID_ARG;
   b->unit_tiles = unit_tiles;
   return NRC_OK;
 }
@@ -435,7 +477,7 @@ nrc_status nrc_batch_autotune(nrc_batch* b, const float* const* records, const i
                               nrc_stream stream, int32_t* chosen) {
   if (!b) return set_error("batch is NULL"), NRC_ERR_INVALID_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const int cand[] = {5, 10, 20, 40, 80, 160};
+  const int cand[] = {0, 5, 10, 20, 40, 80, 160};
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);

@@ -17,6 +17,7 @@ constexpr int kEncDims = 64;    // Table 1: 62 features + 2 pad (Sec. 3.6)
 constexpr int kOutDims = 3;     // RGB
 constexpr int kMaxMats = 9;     // hidden layers <= 8
 constexpr int kTile = 128;      // batch rows per tensor-core tile (MMA M)
+constexpr int kQuerySlots = 5;  // 128-row tiles in flight per SM in the width-64 query kernels
 constexpr int kOutPad = 16;     // output layer padded to N = 16 for the MMA
 constexpr int kMaxBatch = 1 << 16;  // training records per step
 
@@ -299,7 +300,7 @@ inline bool fp16_like(int dtype) { return dtype == NRC_FP16 || dtype == NRC_FP8;
 // One persistent launch over the units of several caches (device arrays);
 // proto supplies the shape, dtype and encoding shared by all of them.
 cudaError_t launch_infer_batched(const Cache* proto, const BatchCache* caches, const BatchUnit* units, int n_units,
-                                 unsigned* counter, int grid, cudaStream_t st);
+                                 unsigned* counter, int grid, cudaStream_t st, const int* unit_off = nullptr);
 cudaError_t launch_train_tc(Cache* c, const float* pool, const float* target, int64_t n_pool, int64_t batch,
                             uint64_t a, uint64_t cc, int step, int* n_partials, float* grad_scale, cudaStream_t st);
 // One training launch over several caches (device array of per-CTA jobs) and

@@ -238,7 +238,7 @@ void nrc_server_default_config(nrc_server_config* c) {
   c->train_steps = 4;
   c->train_batch = 16384;
   c->train_tiles = 4;
-  c->unit_tiles = 20;
+  c->unit_tiles = 0;
 }
 
 int64_t nrc_now_ns(void) { return now_ns(); }
@@ -248,7 +248,7 @@ nrc_status nrc_server_create(const nrc_server_config* cfg, const nrc_config* cac
   *out = nullptr;
   if (cfg->max_viewports < 1 || cfg->max_viewports > 4096 || cfg->max_inflight < 1 || cfg->max_inflight > 64 ||
       cfg->train_steps < 0 || cfg->train_steps > 64 || cfg->train_batch < 0 || cfg->train_batch > 65536 ||
-      cfg->train_tiles < 1 || cfg->train_tiles > 4096 || cfg->unit_tiles < 1 || cfg->unit_tiles > 4096)
+      cfg->train_tiles < 1 || cfg->train_tiles > 4096 || cfg->unit_tiles < 0 || cfg->unit_tiles > 4096)
     return set_error("nrc_server_create: configuration out of range"), NRC_ERR_INVALID_ARG;
   if (cache_cfg->dtype != NRC_FP16 && cache_cfg->dtype != NRC_BF16)
     return set_error("nrc_server_create: served caches compute in FP16 or BF16"), NRC_ERR_UNSUPPORTED;

@@ -8,7 +8,7 @@
 namespace nrc {
 using namespace tc;
 
-constexpr int kSlots = 5;  // 5 x (64 + 32) = 480 of the 512 TMEM columns
+constexpr int kSlots = kQuerySlots;  // 5 x (64 + 32) = 480 of the 512 TMEM columns
 constexpr int kInferThreads = 128 * kSlots;
 constexpr int kTmemCols = 512;
 constexpr int kSlotCols = 96;

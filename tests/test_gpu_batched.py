@@ -50,7 +50,7 @@ def _single(caches, recs):
     return [c.infer(r) if r.shape[0] else torch.empty((0, 3), device=DEV) for c, r in zip(caches, recs)]
 
 
-@pytest.mark.parametrize("unit", [1, 7, 20, 160])
+@pytest.mark.parametrize("unit", [0, 1, 7, 20, 160])
 def test_batch_infer_equals_single_cache(setup, unit):
     caches, recs, _ = setup
     ref = _single(caches, recs)
@@ -86,7 +86,7 @@ def test_batch_autotune_and_graph_replay(setup):
     b = nrc.Batch(caches)
     out = [torch.empty((r.shape[0], 3), device=DEV) for r in recs]
     chosen = b.autotune(recs, out)
-    assert chosen in (5, 10, 20, 40, 80, 160)
+    assert chosen in (0, 5, 10, 20, 40, 80, 160)
     b.infer(recs, out)  # uploads the descriptors for this unit size before capture
     torch.cuda.synchronize()
     g = torch.cuda.CUDAGraph()
