@@ -337,3 +337,48 @@ def test_fused_frame_loss_curve_tracks_the_oracle():
     print("fused fp16 curve: pointwise", pw.max(), "median", mdev, "windows", np.round(wdev, 4), "tol", wtol)
     assert np.all(np.isfinite(got))
     assert pw.max() <= 5e-2 and mdev <= 0.05 and wdev.max() <= wtol
+
+
+@pytest.mark.parametrize("hidden", [1, 2, 3, 4])
+def test_fused_frame_shallow_nets(hidden):
+    """Nets of 2 to 5 matrices through the fused frame with several tiles per training CTA (the tile-boundary
+    scheduling of the weight-gradient MMAs and the buffers they share): queries and the step's gradient within
+    the format tolerance of the oracle, and the gradient equal to the separate launches' within FP32 order."""
+    dims = synth.layer_dims(hidden_layers=hidden)
+    w0 = synth.xavier_weights(dims, seed=600 + hidden)
+    pool, tgt = synth.make_training_pool(16384, seed=601)
+    fs = synth.frame_seed(602, hidden)
+    q = synth.make_records(3000, seed=603)
+    grads = []
+    for ctas in (8, -1):
+        c = nrc.Cache(dtype="fp16", hidden_layers=hidden)
+        c.set_state(w0)
+        c.set_frame_ctas(ctas)
+        if ctas > 0:
+            assert c.frame_ctas(3000, 4096, 1) == 8
+        rgb = torch.empty((3000, 3), device=DEV)
+        c.frame(dev(q), rgb, dev(pool), dev(tgt), 4096, 1, fs)
+        torch.cuda.synchronize()
+        c.check_error()
+        grads.append(c.get_state()[1].astype(np.float64) / 0.1)
+        if ctas > 0:
+            ref_rgb = O.infer(w0, dims, q)
+            EB.format_check(rgb.cpu().numpy(), ref_rgb, EB.emulate_infer(w0, dims, O.encode(q), "fp16"),
+                            label=f"shallow {hidden} queries")
+            st = O.TrainState(w0, dims)
+            _, ref_g = st.step(pool, tgt, 4096, fs, 0, want_grad=True)
+            rec, tg, _ = O.gather(pool, tgt, 4096, fs, 0)
+            EB.format_check(grads[0], ref_g, EB.emulate_16bit(w0, dims, O.encode(rec), tg, "fp16")[1], dims,
+                            label=f"shallow {hidden} gradient")
+    assert np.linalg.norm(grads[0] - grads[1]) <= 1e-4 * np.linalg.norm(grads[1])
+    # three steps in one frame against three separate steps: the same losses within 1e-3
+    ls = []
+    for ctas in (8, -1):
+        c = nrc.Cache(dtype="fp16", hidden_layers=hidden)
+        c.set_state(w0)
+        c.set_frame_ctas(ctas)
+        losses = torch.zeros(3, device=DEV)
+        c.frame(dev(q)[:0], dev(q)[:0], dev(pool), dev(tgt), 4096, 3, fs, loss_out=losses)
+        c.check_error()
+        ls.append(losses.cpu().numpy())
+    assert np.max(np.abs(ls[0] - ls[1]) / ls[1]) <= 1e-3, ls
