@@ -210,3 +210,29 @@ def test_batch_train_step_dev_equals_host_seeds_and_replays_in_a_graph():
         c.close()
     ref_b.close()
     got_b.close()
+
+
+def test_batch_train_more_caches_than_sms():
+    """160 one-tile caches: their training CTAs do not fit one per SM, so the
+    training launches run whole caches in turn; each cache's result equals
+    its training alone, bit for bit (its partition and sums do not depend on
+    the others)."""
+    nc = 160
+    ps, ts = [], []
+    for k in range(nc):
+        p, t = synth.make_training_pool(256, seed=1200 + k)
+        ps.append(dev(p))
+        ts.append(dev(t))
+    fss = [synth.frame_seed(1300 + k, 0) for k in range(nc)]
+    mixed = [nrc.Cache(dtype="fp16", seed=1400 + k) for k in range(nc)]
+    nrc.Batch(mixed).train_step(ps, ts, [128] * nc, fss, 1)
+    torch.cuda.synchronize()
+    for k in range(0, nc, 23):
+        alone = nrc.Cache(dtype="fp16", seed=1400 + k)
+        nrc.Batch([alone]).train_step([ps[k]], [ts[k]], [128], [fss[k]], 1)
+        for x, y in zip(mixed[k].get_state(), alone.get_state()):
+            assert np.array_equal(np.asarray(x), np.asarray(y)), k
+        alone.close()
+    for c in mixed:
+        c.check_error()
+        c.close()
