@@ -202,10 +202,12 @@ NRC_API nrc_status nrc_frame(nrc_cache* cache, const float* queries, int64_t n_q
 
 /* How nrc_frame splits the fused launch: train_ctas = 0 (default) chooses
  * the number of training CTAs per frame from a model of the frame's length
- * (the training's dependent chain against the SM time of all the work);
- * 1 .. SM count fixes it (capped at the batch's 128-row tiles); -1 runs the
- * frame as separate launches (queries, then each step's gradient and Adam
- * kernels).  Host-side setting; INVALID_ARG outside [-1, SM count]. */
+ * (the training's dependent chain against the SM time of all the work), and
+ * runs a frame without queries as separate launches (faster for training
+ * alone); 1 .. SM count fixes it (capped at the batch's 128-row tiles) and
+ * takes the fused launch for frames without queries too; -1 runs every frame
+ * as separate launches (queries, then each step's gradient and Adam kernels).
+ * Host-side setting; INVALID_ARG outside [-1, SM count]. */
 NRC_API nrc_status nrc_set_frame_ctas(nrc_cache* cache, int32_t train_ctas);
 
 /* The number of training CTAs nrc_frame would use for this frame shape, or

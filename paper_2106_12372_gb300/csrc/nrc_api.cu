@@ -437,10 +437,14 @@ nrc_status nrc_train_step(nrc_cache* c, const float* pool, const float* target, 
 
 namespace nrc {
 // The fused frame kernel takes the 16-bit tensor-core path with Adam at
-// width 64 and up to 5 hidden layers.
+// width 64 and up to 5 hidden layers.  A frame without queries runs as
+// separate launches unless the training CTAs are set: alone, the training
+// is faster there (the Adam kernel spreads the reduction over every SM and
+// programmatic dependent launch overlaps the next step's gather).
 static bool fused_frame_ok(const Cache* c, int64_t n_q, int64_t batch, int32_t n_steps) {
   const nrc_config& k = c->cfg;
-  return c->frame_ctas >= 0 && k.path == NRC_PATH_FUSED && (k.dtype == NRC_FP16 || k.dtype == NRC_BF16) &&
+  return c->frame_ctas >= 0 && (n_q > 0 || c->frame_ctas > 0) && k.path == NRC_PATH_FUSED &&
+         (k.dtype == NRC_FP16 || k.dtype == NRC_BF16) &&
          k.optimizer == NRC_OPT_ADAM && k.width == 64 && c->net.n_mats <= 6 && n_steps > 0 && n_steps <= 64 && batch > 0 &&
          (n_q + kTile - 1) / kTile < (int64_t(1) << 31);
 }

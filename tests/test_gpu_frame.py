@@ -64,7 +64,10 @@ def test_frame_split_choice():
     c = nrc.Cache(dtype="fp16")
     t = c.frame_ctas(1920 * 1080, 16384, 4)
     assert 1 <= t <= 128, t
-    assert c.frame_ctas(0, 16384, 4) == 128  # training only: a CTA per tile (up to the SM count)
+    assert c.frame_ctas(0, 16384, 4) == -1  # training only: separate launches unless the CTAs are set
+    c.set_frame_ctas(128)
+    assert c.frame_ctas(0, 16384, 4) == 128
+    c.set_frame_ctas(0)
     assert c.frame_ctas(1000, 300, 4) == 3
     c.set_frame_ctas(-1)
     assert c.frame_ctas(1920 * 1080, 16384, 4) == -1
@@ -260,7 +263,9 @@ def test_fused_frame_training_only_and_query_only():
     q = dev(synth.make_records(3000, seed=542))
     la, lb = torch.zeros(2, device=DEV), torch.zeros(2, device=DEV)
     empty = q[:0]
+    a.set_frame_ctas(32)  # the fused launch with no queries (auto would take separate launches)
     a.frame(empty, empty[:, :3], P, T, 4096, 2, synth.frame_seed(540, 0), loss_out=la)
+    a.set_frame_ctas(0)
     b.frame(empty, empty[:, :3], P, T, 4096, 2, synth.frame_seed(540, 0), loss_out=lb)
     torch.cuda.synchronize()
     assert np.allclose(la.cpu().numpy(), lb.cpu().numpy(), rtol=1e-3)
