@@ -15,7 +15,8 @@
 // batches of the shuffled pool, Sec. 3.5):
 //  - warps 17-19 (producer) gather the CTA's next tile of records through the
 //    shuffle, encode it (Table 1) into a 16-bit swizzled H_0 buffer
-//    (double-buffered) and stage its targets;
+//    (double-buffered) and stage its targets (the launch's first tile: the
+//    compute warpgroups, one row per thread);
 //  - warp 16 (issuer) issues every MMA from one elected thread, with
 //    warp-uniform descriptors, after a named-barrier hand-off from the
 //    compute warpgroups;
@@ -149,6 +150,46 @@ __device__ __forceinline__ void train_grid_barrier(unsigned* ctr, unsigned targe
   named_sync(kBarCompute, kFrameCompute);
 }
 
+// row r of tile i of a training step (Sec. 3.5: the frame's shuffle of the
+// pool; step = the step's index in the shuffled sequence) encoded (Table 1)
+// into H_0 buffer par, its targets and factors into aux
+template <int MODE, bool BF16>
+__device__ __noinline__ void stage_train_row(const float* pool, const float* target, int64_t n_pool, int64_t batch,
+                                           int step, int factor, float pad, int* err, uint8_t* Hb, float* aux,
+                                           int64_t i, int par, int r, uint64_t sh_a, uint64_t sh_c) {
+  const int64_t row = i * kTile + r;
+  float rec[kRecFloats], tg[3] = {0.f, 0.f, 0.f}, fac[3] = {1.f, 1.f, 1.f};
+  if (row < batch) {
+    const uint64_t idx = uint64_t(step) * uint64_t(batch) + uint64_t(row);
+    int64_t src = int64_t((sh_a * idx + sh_c) % uint64_t(n_pool));
+    if (!NRC_DCHECK(src >= 0 && src < n_pool, err)) src = 0;
+    load_record(pool, src, rec);
+    tg[0] = __ldg(target + src * 3);
+    tg[1] = __ldg(target + src * 3 + 1);
+    tg[2] = __ldg(target + src * 3 + 2);
+    if (factor) {
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) fac[ch] = rec[8 + ch] + rec[11 + ch];
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < kRecFloats; ++k) rec[k] = 0.0f;
+  }
+  float f[kEncDims];
+  encode_record<MODE>(rec, pad, f);
+  uint8_t* h0 = Hb + par * 16384;
+#pragma unroll
+  for (int c4 = 0; c4 < 4; ++c4) {
+    uint32_t pk[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) pk[k] = pack2<BF16, false>(f[16 * c4 + 2 * k], f[16 * c4 + 2 * k + 1]);
+    store_q_sw128(h0, r, 2 * c4, pk);
+  }
+  float* ax = aux + (par * kTile + r) * 8;
+  ax[0] = tg[0], ax[1] = tg[1], ax[2] = tg[2], ax[3] = fac[0], ax[4] = fac[1], ax[5] = fac[2];
+}
+
+
 template <int MODE, bool BF16>
 __device__ __forceinline__ void frame_train(const FrameParams& p, const TrainView& tv, const int b, uint8_t* sw,
                                             uint32_t tmem, uint64_t* bar_w,
@@ -166,50 +207,27 @@ __device__ __forceinline__ void frame_train(const FrameParams& p, const TrainVie
   auto hbuf = [&](int l, int par) { return l == 0 ? par : 1 + l; };
   auto dbuf = [&](int l) { return l == L ? 7 : l == L - 1 ? 8 : l == L - 2 ? 9 : 1 + (l + 2); };
 
+  auto stage_row = [&](int64_t i, int s, int par, int r, uint64_t sh_a, uint64_t sh_c) {
+    stage_train_row<MODE, BF16>(tv.pool, tv.target, tv.n_pool, tv.batch, tv.step0 + s, p.factor, p.pad, p.err, Hb, aux, i,
+                                par, r, sh_a, sh_c);
+  };
+
   if (warp > kIssuerWarp) {
     // ------------------------------------------------------------ producer
     uint64_t sh_a = tv.a, sh_c = tv.c;
     if (tv.seed) lcg_shuffle(tv.n_pool, *tv.seed, &sh_a, &sh_c);  // the frame seed lives on the device
-    // three warps gather, encode and stage each tile's 128 rows (rows pt and
-    // pt + 96), then arrive on the tile's full barrier
+    // three warps stage each tile's 128 rows (rows pt and pt + 96), then
+    // arrive on the tile's full barrier; the launch's first tile is staged
+    // by the compute warpgroups (one row per thread) while these stage the
+    // second
     const int pt = tid - (kIssuerWarp + 1) * 32;
     int j = 0;
     for (int s = 0; s < p.n_steps; ++s) {
       for (int64_t i = b; i < tiles; i += T, ++j) {
+        if (j == 0) continue;
         const int par = j & 1;
         if (j >= 2) mbar_wait(&bar_free[par], uint32_t(((j - 2) >> 1) & 1), p.err);
-        for (int r = pt; r < kTile; r += kProducerThreads) {
-          const int64_t row = i * kTile + r;
-          float rec[kRecFloats], tg[3] = {0.f, 0.f, 0.f}, fac[3] = {1.f, 1.f, 1.f};
-          if (row < tv.batch) {
-            const uint64_t idx = uint64_t(tv.step0 + s) * uint64_t(tv.batch) + uint64_t(row);
-            int64_t src = int64_t((sh_a * idx + sh_c) % uint64_t(tv.n_pool));
-            if (!NRC_DCHECK(src >= 0 && src < tv.n_pool, p.err)) src = 0;
-            load_record(tv.pool, src, rec);
-            tg[0] = __ldg(tv.target + src * 3);
-            tg[1] = __ldg(tv.target + src * 3 + 1);
-            tg[2] = __ldg(tv.target + src * 3 + 2);
-            if (p.factor) {
-#pragma unroll
-              for (int ch = 0; ch < 3; ++ch) fac[ch] = rec[8 + ch] + rec[11 + ch];
-            }
-          } else {
-#pragma unroll
-            for (int k = 0; k < kRecFloats; ++k) rec[k] = 0.0f;
-          }
-          float f[kEncDims];
-          encode_record<MODE>(rec, p.pad, f);
-          uint8_t* h0 = Hb + par * 16384;
-#pragma unroll
-          for (int c4 = 0; c4 < 4; ++c4) {
-            uint32_t pk[8];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) pk[k] = pack2<BF16, false>(f[16 * c4 + 2 * k], f[16 * c4 + 2 * k + 1]);
-            store_q_sw128(h0, r, 2 * c4, pk);
-          }
-          float* ax = aux + (par * kTile + r) * 8;
-          ax[0] = tg[0], ax[1] = tg[1], ax[2] = tg[2], ax[3] = fac[0], ax[4] = fac[1], ax[5] = fac[2];
-        }
+        for (int r = pt; r < kTile; r += kProducerThreads) stage_row(i, s, par, r, sh_a, sh_c);
         fence_proxy_async_smem();
         mbar_arrive(&bar_full[par]);
       }
@@ -388,12 +406,25 @@ __device__ __forceinline__ void frame_train(const FrameParams& p, const TrainVie
     }
   };
   const bool lanes_lo = (warp & 3) < 2;  // this warp's TMEM lanes are 0..63
+  float w1 = 0.f, m1 = 0.f, v1 = 0.f, e1 = 0.f;  // the Adam state of the thread's parameter
 
   for (int s = 0; s < p.n_steps; ++s) {
     if (tid == 0) {
       fence_proxy_async_global();
       mbar_arrive_expect_tx(bar_w, uint32_t(p.img_bytes));
       bulk_g2s(sw, s == 0 ? tv.img_in : tv.img_work, uint32_t(p.img_bytes), bar_w);
+    }
+    if (s == 0) {
+      // the launch's first tile, one row per thread: the chain waits for one
+      // round of record loads instead of the producer's two
+      if (tid < kTile) {
+        uint64_t sh_a = tv.a, sh_c = tv.c;
+        if (tv.seed) lcg_shuffle(tv.n_pool, *tv.seed, &sh_a, &sh_c);
+        stage_row(b, 0, 0, tid, sh_a, sh_c);
+        fence_proxy_async_smem();
+      }
+      named_sync(kBarCompute, kFrameCompute);
+      if (tid < kProducerThreads) mbar_arrive(&bar_full[0]);  // the count the producer warps would give
     }
     float loss_acc = 0.0f;
     for (int64_t i = b; i < tiles; i += T, ++j) {
@@ -527,8 +558,9 @@ __device__ __forceinline__ void frame_train(const FrameParams& p, const TrainVie
       if (q == 0 && (tid & 31) == 0) red[warp] = sl;
     }
     // CTA b owns the partial quads [q_lo, q_hi); thread tid finishes element
-    // tid % 4 of quad tid / 4 and loads that parameter's state now, before
-    // the barrier
+    // tid % 4 of quad tid / 4.  With one element per thread the thread keeps
+    // that parameter's state in registers from step to step: loaded before
+    // the first step's barrier, written back by the launch's last step
     const int QT = (p.net.n_params + 3) / 4;
     const int q_lo = int((long long)b * QT / T), q_hi = int((long long)(b + 1) * QT / T);
     const int Qb = q_hi - q_lo;
@@ -540,7 +572,6 @@ __device__ __forceinline__ void frame_train(const FrameParams& p, const TrainVie
       l_out = l;
       return p.net.w_off[l] + (loc % R) * 64 + 4 * (loc / R) + e;
     };
-    float w1 = 0.f, m1 = 0.f, v1 = 0.f, e1 = 0.f;
     int pi = -1, li = 0;
     auto load_state = [&](int Qp, int e) {
       pi = param_of(Qp, e, li);
@@ -553,9 +584,10 @@ __device__ __forceinline__ void frame_train(const FrameParams& p, const TrainVie
     };
     const bool one_each = 4 * Qb <= kFrameCompute;
     // the slice's weights, moments (and average) come into shared memory by
-    // cp.async while the barrier runs: quad qd of array a at st_state[a][qd]
+    // cp.async while the first step's barrier runs: quad qd of array a at
+    // st_state[a][qd]
     float4* st_state = reinterpret_cast<float4*>(Hb + 3 * 16384);  // [4][Qb], Qb <= 128
-    if (one_each && tid < 4 * Qb) {
+    if (one_each && s == 0 && tid < 4 * Qb) {
       const int a = tid / Qb, qd = tid % Qb;
       const float* arr = a == 0 ? tv.w : a == 1 ? tv.m : a == 2 ? tv.v : tv.ema;
       if (arr) {
@@ -612,14 +644,19 @@ __device__ __forceinline__ void frame_train(const FrameParams& p, const TrainVie
     }
     cp_async_wait<0>();  // this thread's state quads have landed
     named_sync(kBarCompute, kFrameCompute);
+    // the parameters' fp32 state goes to global memory once per launch
+    // when each thread keeps its parameter's state in registers
+    const bool write_state = !one_each || s + 1 == p.n_steps;
     auto adam1 = [&](float g) {  // the loaded parameter's step (pi < n_params)
       g *= tv.inv3n;
       m1 = fmaf(p.b1, m1, (1.0f - p.b1) * g);
       v1 = fmaf(p.b2, v1, (1.0f - p.b2) * g * g);
       w1 = w1 - p.lr * (m1 / c1) / (sqrtf(v1 / c2) + p.eps);
-      tv.w[pi] = w1;
-      tv.m[pi] = m1;
-      tv.v[pi] = v1;
+      if (write_state) {
+        tv.w[pi] = w1;
+        tv.m[pi] = m1;
+        tv.v[pi] = v1;
+      }
       const int qq = pi - p.net.w_off[li];
       uint32_t off = uint32_t(p.img.off[li]) + sw128_offset(uint32_t(qq / 64), uint32_t(qq % 64));
       if (!NRC_DCHECK(off + 2 <= uint32_t(p.img_bytes), p.err)) off = 0;
@@ -630,7 +667,7 @@ __device__ __forceinline__ void frame_train(const FrameParams& p, const TrainVie
       if (tv.ema) {
         // the weight average of Eq. 2 (bias-corrected reading); never read by training
         e1 = ((1.0f - p.alpha) * w1 + p.alpha * eta_prev * e1) / eta;
-        tv.ema[pi] = e1;
+        if (write_state) tv.ema[pi] = e1;
         if (BF16)
           *reinterpret_cast<__nv_bfloat16*>(tv.img_ema_work + off) = __float2bfloat16_rn(e1);
         else
@@ -639,12 +676,14 @@ __device__ __forceinline__ void frame_train(const FrameParams& p, const TrainVie
     };
     if (one_each) {
       if (tid < 4 * Qb) {
-        const float* sst = reinterpret_cast<const float*>(st_state);
         pi = param_of(q_lo + tid / 4, tid % 4, li);
-        w1 = sst[tid];
-        m1 = sst[4 * Qb + tid];
-        v1 = sst[8 * Qb + tid];
-        if (tv.ema) e1 = sst[12 * Qb + tid];
+        if (s == 0) {
+          const float* sst = reinterpret_cast<const float*>(st_state);
+          w1 = sst[tid];
+          m1 = sst[4 * Qb + tid];
+          v1 = sst[8 * Qb + tid];
+          if (tv.ema) e1 = sst[12 * Qb + tid];
+        }
       }
       if (tid < 4 * Qb && pi < p.net.n_params) {
         const float* sc = reinterpret_cast<const float*>(scratch);
