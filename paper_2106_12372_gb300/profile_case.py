@@ -3,10 +3,13 @@
     python -m paper_2106_12372_gb300.profile_case --what infer --n 2073600 --dtype fp16 --iters 3
     python -m paper_2106_12372_gb300.profile_case --what train --batch 16384 --dtype fp16 --iters 3
     python -m paper_2106_12372_gb300.profile_case --what frame --n 2073600 --steps 4 --iters 3
+    python -m paper_2106_12372_gb300.profile_case --what train-fused --batch 16384 --steps 4 --ctas 43 --iters 3
     python -m paper_2106_12372_gb300.profile_case --what infer --net-width 128 --hidden 7 --dtype fp16
     python -m paper_2106_12372_gb300.profile_case --what paths --width 1920 --height 1080 --iters 3
 
-``paths`` runs the training-record pipeline around the query (terminate, the
+``train-fused`` runs a frame without queries through the frame kernel's
+training role on --ctas CTAs (a frame without queries otherwise takes the
+separate gradient and Adam launches).  ``paths`` runs the training-record pipeline around the query (terminate, the
 render and tail queries, the self-training records, 4 training steps, the
 composite) on synthetic 10-vertex paths: a quarter-resolution path set tiled
 4 x 4 over the frame, training tiles of 8 x 8 pixels.
@@ -22,7 +25,7 @@ from paper_2106_12372_gb300 import build, nrc, synth
 
 def main() -> None:
     ap = argparse.ArgumentParser()
-    ap.add_argument("--what", choices=["infer", "train", "frame", "paths"], default="infer")
+    ap.add_argument("--what", choices=["infer", "train", "train-fused", "frame", "paths"], default="infer")
     ap.add_argument("--width", type=int, default=1920)
     ap.add_argument("--height", type=int, default=1080)
     ap.add_argument("--n", type=int, default=1920 * 1080)
@@ -32,6 +35,7 @@ def main() -> None:
     ap.add_argument("--iters", type=int, default=3)
     ap.add_argument("--net-width", type=int, default=64, help="64, or 128 (with --hidden 7) for the wide network")
     ap.add_argument("--hidden", type=int, default=5)
+    ap.add_argument("--ctas", type=int, default=43, help="training CTAs of --what train-fused")
     args = ap.parse_args()
     build.build()
     dev = torch.device("cuda:0")
@@ -41,10 +45,14 @@ def main() -> None:
     cache = nrc.Cache(dtype=args.dtype, width=args.net_width, hidden_layers=args.hidden)
     pool_np, tgt_np = synth.make_training_pool(args.batch * args.steps, seed=5)
     pool, tgt = torch.from_numpy(pool_np).to(dev), torch.from_numpy(tgt_np).to(dev)
-    rec = torch.from_numpy(synth.make_records(args.n, seed=6)).to(dev) if args.what != "train" else None
+    rec = torch.from_numpy(synth.make_records(args.n, seed=6)).to(dev) if not args.what.startswith("train") else None
     rgb = torch.empty((args.n, 3), device=dev) if rec is not None else None
+    if args.what == "train-fused":
+        cache.set_frame_ctas(args.ctas)
+        q0 = torch.zeros((1, 16), device=dev)
+        rec, rgb = q0[:0], q0[:0, :3]
     for it in range(args.iters):
-        if args.what == "frame":  # the fused frame: one launch of queries and training steps
+        if args.what in ("frame", "train-fused"):  # the fused frame: one launch of queries and training steps
             cache.frame(rec, rgb, pool, tgt, args.batch, args.steps, synth.frame_seed(5, it))
         if args.what == "infer":
             cache.infer(rec, rgb)
