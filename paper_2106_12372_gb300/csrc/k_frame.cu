@@ -830,11 +830,31 @@ __global__ void __launch_bounds__(kFrameThreads, 1) k_frame_tc(const __grid_cons
     __syncthreads();
     fence_after();
     uint32_t phase = 0;
+    // A slot retires when it starts its last tile (its next ticket is past
+    // the end, so it draws no more): one count on sync[2].  The slot that
+    // retires last over the grid zeroes the counters for the next launch once
+    // its tile is done; the launch's end then waits for no atomic.
+    const unsigned n_slots_all = gridDim.x * unsigned(kSlots);
+    auto reset_counters = [&]() {
+      p.sync[0] = 0u;
+      p.sync[1] = 0u;
+      p.sync[2] = 0u;
+      p.sync[3] = 0u;
+    };
+    if (cur >= n_tiles && rit == lead_t && atomicAdd(&p.sync[2], 1u) + 1u == n_slots_all) reset_counters();
     while (cur < n_tiles) {
       const int64_t row = cur * kTile + rit;
       prefetch(nxt, buf ^ 1);
       int nxt2 = 0;
-      if (rit == lead_t) nxt2 = int(atomicAdd(&p.sync[1], 1u));
+      unsigned retired = 0u;  // the slot's retire count + 1 (lead thread, last tile)
+      if (rit == lead_t) {
+        if (nxt < n_tiles) {
+          nxt2 = int(atomicAdd(&p.sync[1], 1u));
+        } else {
+          nxt2 = int(n_tiles);
+          retired = atomicAdd(&p.sync[2], 1u) + 1u;
+        }
+      }
       cp_async_wait<1>();
       float r[kRecFloats];
       rs.read(buf, r);
@@ -845,6 +865,7 @@ __global__ void __launch_bounds__(kFrameThreads, 1) k_frame_tc(const __grid_cons
                         row < p.n_q ? p.rgb + row * 3 : nullptr, fac_row, rs.rot, [&]() {
                           if (rit == lead_t) s_next[slot] = nxt2;
                         });
+      if (retired == n_slots_all) reset_counters();
       cur = nxt;
       nxt = s_next[slot];
     }
@@ -852,19 +873,20 @@ __global__ void __launch_bounds__(kFrameThreads, 1) k_frame_tc(const __grid_cons
   }
 
   // ------------------------------------------------------------ retire
+  // (with queries the slots retired above)
   fence_before();
   __syncthreads();
-  if (tid == 0) {
+  if (tid == 0 && n_tiles == 0) {
     __threadfence();
     const unsigned old = atomicAdd(&p.sync[2], 1u);
     s_last = old + 1 == gridDim.x;
     if (s_last) __threadfence();
   }
   __syncthreads();
-  if (s_last) {
+  if (n_tiles == 0 && s_last) {
     // every CTA is done: without queries the training's images replace the
     // cache's now; the counters are zero again for the next launch
-    if (n_tiles == 0 && p.n_train > 0 && p.n_steps > 0) copy_images(p);
+    if (p.n_train > 0 && p.n_steps > 0) copy_images(p);
     __syncthreads();
     if (tid == 0) {
       p.sync[0] = 0u;
